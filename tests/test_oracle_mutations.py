@@ -1,0 +1,91 @@
+"""Planted mistakes: each mutant of the oracle (a copy of its C source with
+one plausible bug) must fail at least one pin of test_oracle_pins.py.
+
+The mutants are built on the CPU from a temporary copy; the oracle source in
+the repository is never modified.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+import tests.test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lasso_oracle.c")
+
+# (name, original text, mutated text) -- each original occurs in the source
+MUTANTS = [
+    ("primal drops lambda", "double P = 0.5 * rr + lambda * l1;", "double P = 0.5 * rr + l1;"),
+    ("dual drops lambda", "double d = lambda * (alpha * rho[i]) - y[i];",
+     "double d = (alpha * rho[i]) - y[i];"),
+    ("soft-threshold sign", "(b > 0.0 ? ab - thr : -(ab - thr))", "(b > 0.0 ? -(ab - thr) : ab - thr)"),
+    ("gradient sign", "double b = beta[j] + g / n2;", "double b = beta[j] - g / n2;"),
+    ("residual update sign", "for (int64_t i = 0; i < n; ++i) rho[i] -= d * x[i];",
+     "for (int64_t i = 0; i < n; ++i) rho[i] += d * x[i];"),
+    ("threshold uses norm not squared norm", "double thr = lambda / n2;", "double thr = lambda / sqrt(n2);"),
+    ("check correlates y instead of rho", "double cj = in_scope ? dot_col(X, ldx, n, j, rho) : 0.0;",
+     "double cj = in_scope ? dot_col(X, ldx, n, j, y) : 0.0;"),
+    ("sphere test reversed", "if (mu < 1.0) mask_clear(mask_out, j);", "if (mu > 1.0) mask_clear(mask_out, j);"),
+    ("radius divided twice by lambda", "double r = sqrt(2.0 * Gs) / lambda;",
+     "double r = sqrt(2.0 * Gs) / (lambda * lambda);"),
+    ("radius without gap", "double Gs = (G > 0.0 ? G : 0.0) + tau;", "double Gs = tau;"),
+    ("dual scaling ignores lambda", "alpha = 1.0 / (lambda > m ? lambda : m);", "alpha = 1.0 / m;"),
+    ("grid off by one", "pow(10.0, -delta * (double)t / (double)(T - 1))",
+     "pow(10.0, -delta * (double)(t + 1) / (double)(T - 1))"),
+    ("column stride transposed", "const double* x = X + j * ldx;\n  double s = 0.0;",
+     "const double* x = X + j;\n  double s = 0.0;"),
+    ("screened coefficient not removed from residual", "for (int64_t i = 0; i < n; ++i) rho[i] += b * X[i + j * ldx];",
+     "(void)b;"),
+    ("Eq. (8) clipped to the wrong side", "if (a < -lim) a = -lim;", "if (a < -lim) a = lim;"),
+    ("lambda_max from the smallest correlation", "if (fabs(c0[j]) > lmax) { lmax = fabs(c0[j]); arg = j; }",
+     "if (j == 0 || fabs(c0[j]) < lmax) { lmax = fabs(c0[j]); arg = j; }"),
+]
+
+PIN_CALLS = [
+    (pins.test_grid_is_geometric, {}),
+    (pins.test_hand_example_identity_design, {}),
+    (pins.test_lambda_max_and_zero_solution, {}),
+    (pins.test_first_feature_enters_linearly, {}),
+    (pins.test_orthonormal_soft_threshold, {"seed": 3}),
+    (pins.test_bad_warm_start_reaches_optimum, {}),
+    (pins.test_screening_a_nonzero_coefficient, {}),
+    (pins.test_bruteforce_agreement, {"seed": 5, "n": 20, "p": 8}),
+    (pins.test_kkt_at_tight_solution, {}),
+    (pins.test_every_sphere_contains_dual_optimum, {}),
+    (pins.test_screened_features_are_zero, {}),
+    (pins.test_finite_identification, {}),
+    (pins.test_prop3_sequential_identity, {}),
+    (pins.test_dual_point_eq8_is_projection_on_span, {}),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir():
+    d = tempfile.mkdtemp(prefix="oracle_mut_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("name,orig,mut", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(workdir, monkeypatch, name, orig, mut):
+    src = open(SRC).read()
+    assert src.count(orig) >= 1, f"mutation anchor not found: {orig!r}"
+    msrc = src.replace(orig, mut, 1)
+    idx = MUTANTS.index((name, orig, mut))
+    cpath = os.path.join(workdir, f"mut{idx}.c")
+    so = os.path.join(workdir, f"libmut{idx}.so")
+    open(cpath, "w").write(msrc)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
+                           "-o", so, cpath, "-lm"])
+    monkeypatch.setattr(oracle, "_lib", oracle._bind(so))
+    caught = None
+    for fn, kw in PIN_CALLS:
+        try:
+            fn(oracle, **kw)
+        except Exception as e:  # noqa: BLE001 -- any failure of a pin counts
+            caught = f"{fn.__name__}: {type(e).__name__}"
+            break
+    assert caught, f"mutant '{name}' passed every pin"
