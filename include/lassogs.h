@@ -1,0 +1,142 @@
+/*
+ * lassogs -- Lasso paths by cyclic coordinate descent with GAP SAFE sphere
+ * screening on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Fercoq, Gramfort, Salmon, "Mind the duality gap: safer rules for
+ * the Lasso", ICML 2015 (arXiv:1505.03410).  The solver is Algorithm 1 of
+ * Sec. 4.1: coordinate descent over the safe-active set, a GAP SAFE sphere
+ * check (Eq. (10)) every f passes, warm starts along the geometric grid of
+ * Sec. 3.3, stop when the duality gap (Sec. 3.2) is <= eps.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are device pointers (global memory of the current
+ *     CUDA device); pointers named *_host are host pointers.
+ *   - The caller owns every buffer.  The library allocates no memory: the
+ *     scratch it needs is the caller-provided workspace, whose size is given
+ *     by the matching *_workspace_size function.
+ *   - Designs are column-major: element (i, j) of X is X[i + j*ldx].
+ *   - Calls that take a stream enqueue their work on it and return without
+ *     waiting; results are valid once the stream has been synchronised.
+ *     The return value reports argument and launch errors only.  Per-lambda
+ *     convergence and device-side errors are written into the stats records.
+ *   - No call aborts, exits or traps.  On error the call returns a non-zero
+ *     lasso_status and lasso_last_error() describes it (thread-local).
+ *   - The mask of safe-active features uses one bit per feature: bit (j % 32)
+ *     of 32-bit word j / 32; words = ceil(p / 32).
+ */
+#ifndef LASSOGS_H
+#define LASSOGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LASSOGS_ABI_VERSION 1
+
+typedef enum lasso_status {
+  LASSO_OK = 0,
+  LASSO_ERR_INVALID_ARG = 1,  /* a size, pointer, alignment or option is invalid */
+  LASSO_ERR_NONFINITE = 2,    /* X or y holds NaN or Inf (detected by the precompute) */
+  LASSO_ERR_WORKSPACE = 3,    /* workspace NULL, misaligned or smaller than required */
+  LASSO_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in lasso_last_error) */
+  LASSO_ERR_NOT_CONVERGED = 5,/* a lambda reached the pass cap K before gap <= eps */
+  LASSO_ERR_TIMEOUT = 6       /* a device-side wait hit its time limit (never expected) */
+} lasso_status;
+
+typedef enum lasso_dtype {
+  LASSO_F64 = 0,   /* IEEE binary64 */
+  LASSO_F32 = 1,   /* IEEE binary32 */
+  LASSO_BF16 = 2   /* bfloat16 */
+} lasso_dtype;
+
+/* Solver options.  Fill with lasso_default_opts() and override fields. */
+typedef struct lasso_opts {
+  int32_t screen_period; /* f: passes between two GAP SAFE checks (Sec. 4.1 uses 10); >= 1 */
+  int32_t dual_point;    /* 0: theta = rho / max(lambda, ||X^T rho||_inf) (default);
+                            1: the clipped optimal scaling of Eq. (8) */
+  int32_t xtr_scope;     /* 0: X^T rho over all p features at every check (default);
+                            1: over the safe-active features only (the O(nq) check of Sec. 4.1) */
+  int32_t warm_start;    /* 1: beta carried from lambda_{t-1} to lambda_t (Sec. 3.3, default);
+                            0: every lambda starts from beta0 (or 0) */
+  int64_t max_epochs;    /* K: passes allowed per lambda (Algorithm 1 INPUT), default 100000 */
+  double gap_tol_rel;    /* eps / ||y||^2: stop when gap <= gap_tol_rel * ||y||^2, default 1e-6 */
+  int32_t gemm_dtype;    /* batched solver: input type of the tensor-core X^T R product at the
+                            first check of each lambda (LASSO_BF16 default; LASSO_F32 = exact
+                            CUDA-core product); ignored by lasso_path */
+  int32_t reserved[3];   /* must be zero */
+} lasso_opts;
+
+/* Per-lambda record written by the solvers (device memory, one per lambda). */
+typedef struct lasso_path_stats {
+  double lambda;     /* lambda_t = lambda_max * ratio_t */
+  double primal;     /* P_lambda(beta) at the last check, Eq. (1) */
+  double dual;       /* D_lambda(theta) at the last check, Eq. (2) */
+  double gap;        /* primal - dual at the last check (Sec. 3.2) */
+  double radius;     /* GAP SAFE radius sqrt(2 gap)/lambda of the last check (Prop. 1) */
+  double alpha;      /* dual scaling of the last check: theta = alpha * rho */
+  int64_t epochs;    /* coordinate-descent passes run at this lambda */
+  int64_t checks;    /* GAP SAFE checks run at this lambda */
+  int64_t n_active;  /* features kept by the last check (|A|, Eq. (6)) */
+  int64_t n_nonzero; /* nonzero coefficients of the returned beta */
+  int32_t converged; /* 1 if gap <= eps was reached */
+  int32_t status;    /* lasso_status of this lambda (OK, NOT_CONVERGED, TIMEOUT, NONFINITE) */
+} lasso_path_stats;
+
+/* Fills *opts with the defaults listed above.  opts must not be NULL. */
+void lasso_default_opts(lasso_opts* opts);
+
+/* The geometric grid of Sec. 3.3 as ratios to lambda_max:
+ * ratios_host[t] = 10^(-delta * t / (T - 1)), t = 0..T-1 (ratios_host[0] = 1;
+ * T == 1 gives {1}).  Host-only, synchronous.  INVALID_ARG if T < 1,
+ * delta < 0 or ratios_host is NULL. */
+lasso_status lasso_lambda_grid(int32_t T, double delta, double* ratios_host);
+
+/* Bytes of device workspace lasso_path needs for these sizes (0 when the
+ * sizes are invalid).  The workspace must be 256-byte aligned. */
+size_t lasso_path_workspace_size(int64_t n, int64_t p, lasso_dtype x_dtype, const lasso_opts* opts);
+
+/* One Lasso path by Algorithm 1 (CD with GAP SAFE sphere rules).
+ *
+ *   X_dev        n x p design, column-major, leading dimension ldx.
+ *                x_dtype LASSO_F32: ldx % 4 == 0 and X_dev 16-byte aligned.
+ *                x_dtype LASSO_F64: ldx >= n, X_dev 8-byte aligned.
+ *   n, p         1 <= n <= 2048, 1 <= p < 2^31.
+ *   y_dev        n responses, FP64.
+ *   lambda_ratios_dev  T ratios lambda_t / lambda_max, each in (0, 1]
+ *                (lambda_max = ||X^T y||_inf is computed on the device);
+ *                lasso_lambda_grid gives the grid of Sec. 3.3.
+ *   beta0_dev    p starting coefficients (FP64) or NULL for zeros.
+ *   opts         NULL for the defaults.
+ *   beta_out_dev p x T FP64, column t = solution at lambda_t.
+ *   mask_out_dev words x T uint32: the safe-active set of the last check at
+ *                lambda_t, or NULL.
+ *   stats_dev    T lasso_path_stats records.
+ *   workspace_dev, workspace_bytes  device scratch of at least
+ *                lasso_path_workspace_size(n, p, x_dtype, opts) bytes.
+ *   stream       a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Arithmetic: the per-check X^T rho pass runs in FP32 with a rigorous
+ * forward-error bound; features whose test or maximum the bound leaves
+ * undecided are recomputed exactly.  Coordinate updates keep beta and rho
+ * in double-float (pairs of FP32, about 48 significand bits) with exact
+ * integer reductions; objectives, gap and radius are FP64.
+ *
+ * Returns LASSO_OK once the work is enqueued.  The work uses every SM of the
+ * device for its duration (one cooperative launch). */
+lasso_status lasso_path(const void* X_dev, lasso_dtype x_dtype, int64_t n, int64_t p, int64_t ldx,
+                        const double* y_dev, const double* lambda_ratios_dev, int32_t T,
+                        const double* beta0_dev, const lasso_opts* opts,
+                        double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
+                        void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Thread-local description of the last error returned on this thread
+ * ("" if none).  The pointer stays valid until the next call on the thread. */
+const char* lasso_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LASSOGS_H */

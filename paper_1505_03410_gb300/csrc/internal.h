@@ -1,0 +1,30 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lassogs.h"
+
+namespace lassogs {
+
+constexpr int64_t kMaxRows = 2048;  // rows n supported by the register-resident residual
+
+// records the thread-local message and returns code
+lasso_status set_error(lasso_status code, const char* fmt, ...);
+void clear_error();
+
+size_t path_workspace_size(int64_t n, int64_t p, lasso_dtype xt, int64_t ldx);
+lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, int64_t ldx, const double* y,
+                         const double* ratios, int32_t T, const double* beta0, const lasso_opts& o,
+                         double* beta_out, uint32_t* mask_out, lasso_path_stats* stats, void* ws, size_t ws_bytes,
+                         cudaStream_t stream);
+
+}  // namespace lassogs
+
+#define CUDA_TRY(call)                                                                                   \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess)                                                                               \
+      return ::lassogs::set_error(LASSO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+  } while (0)

@@ -1,0 +1,165 @@
+"""ctypes binding of liblassogs (include/lassogs.h).
+
+The functions below carry the C names and only marshal arguments: every step
+of the solver runs in the CUDA library.  There is no CPU fallback -- if the
+library is missing, loading it raises.
+
+``solve_path`` is a convenience wrapper that allocates the outputs and the
+workspace as torch CUDA tensors (PyTorch supplies device memory and streams)
+and calls ``lasso_path`` on the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblassogs.so")
+
+LASSO_OK = 0
+LASSO_ERR_INVALID_ARG = 1
+LASSO_ERR_NONFINITE = 2
+LASSO_ERR_WORKSPACE = 3
+LASSO_ERR_CUDA = 4
+LASSO_ERR_NOT_CONVERGED = 5
+LASSO_ERR_TIMEOUT = 6
+LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
+
+# every symbol include/lassogs.h declares
+EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
+            "lasso_last_error")
+
+
+class LassoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"lasso status {status}: {msg}")
+        self.status = status
+
+
+class LassoOpts(ctypes.Structure):
+    _fields_ = [("screen_period", ctypes.c_int32), ("dual_point", ctypes.c_int32),
+                ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
+                ("gemm_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class LassoPathStats(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("primal", ctypes.c_double), ("dual", ctypes.c_double),
+                ("gap", ctypes.c_double), ("radius", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("epochs", ctypes.c_int64), ("checks", ctypes.c_int64), ("n_active", ctypes.c_int64),
+                ("n_nonzero", ctypes.c_int64), ("converged", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+STATS_DTYPE = np.dtype([("lambda", "<f8"), ("primal", "<f8"), ("dual", "<f8"), ("gap", "<f8"),
+                        ("radius", "<f8"), ("alpha", "<f8"), ("epochs", "<i8"), ("checks", "<i8"),
+                        ("n_active", "<i8"), ("n_nonzero", "<i8"), ("converged", "<i4"), ("status", "<i4")])
+assert STATS_DTYPE.itemsize == ctypes.sizeof(LassoPathStats)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblassogs.so (built by paper_1505_03410_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} is missing: build it with paper_1505_03410_gb300.build.build()")
+            lib = ctypes.CDLL(p)
+            V, I32, I64, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+            lib.lasso_default_opts.argtypes = [ctypes.POINTER(LassoOpts)]
+            lib.lasso_default_opts.restype = None
+            lib.lasso_lambda_grid.argtypes = [I32, D, V]
+            lib.lasso_lambda_grid.restype = ctypes.c_int
+            lib.lasso_path_workspace_size.argtypes = [I64, I64, ctypes.c_int, ctypes.POINTER(LassoOpts)]
+            lib.lasso_path_workspace_size.restype = SZ
+            lib.lasso_path.argtypes = [V, ctypes.c_int, I64, I64, I64, V, V, I32, V, ctypes.POINTER(LassoOpts),
+                                       V, V, V, V, SZ, V]
+            lib.lasso_path.restype = ctypes.c_int
+            lib.lasso_last_error.argtypes = []
+            lib.lasso_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def lasso_last_error() -> str:
+    return load().lasso_last_error().decode()
+
+
+def _check(status):
+    if status != LASSO_OK:
+        raise LassoError(status, lasso_last_error())
+    return status
+
+
+def lasso_default_opts(**overrides) -> LassoOpts:
+    o = LassoOpts()
+    load().lasso_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def lasso_lambda_grid(T: int, delta: float) -> np.ndarray:
+    out = np.empty(int(T), dtype=np.float64)
+    _check(load().lasso_lambda_grid(int(T), float(delta), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def lasso_path_workspace_size(n: int, p: int, x_dtype: int, opts: LassoOpts | None = None) -> int:
+    return int(load().lasso_path_workspace_size(int(n), int(p), int(x_dtype),
+                                                ctypes.byref(opts) if opts is not None else None))
+
+
+def lasso_path(X, x_dtype, n, p, ldx, y, lambda_ratios, T, beta0, opts, beta_out, mask_out, stats,
+               workspace, workspace_bytes, stream) -> int:
+    """Direct call of the C entry point; pointer arguments are integers
+    (device addresses) or None.  Raises LassoError on a non-zero status."""
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    return _check(load().lasso_path(vp(X), int(x_dtype), int(n), int(p), int(ldx), vp(y), vp(lambda_ratios),
+                                    int(T), vp(beta0), ctypes.byref(opts) if opts is not None else None,
+                                    vp(beta_out), vp(mask_out), vp(stats), vp(workspace), int(workspace_bytes),
+                                    vp(stream)))
+
+
+def stats_to_numpy(stats_tensor) -> np.ndarray:
+    """A uint8 torch tensor of T * sizeof(stats) bytes -> structured numpy array."""
+    return stats_tensor.cpu().numpy().view(STATS_DTYPE)
+
+
+def solve_path(XT, y, ratios, n=None, beta0=None, opts=None, workspace=None, stream=None, want_mask=True):
+    """Allocate outputs as torch CUDA tensors and run lasso_path.
+
+    XT: (p, ldx) contiguous CUDA tensor (float32 or float64) -- the column-major
+    design; y: (n,) float64 CUDA tensor; ratios: (T,) float64 CUDA tensor.
+    Returns a dict with beta (T, p) float64, mask (T, words) int32 view of the
+    uint32 words, stats (uint8 bytes; see stats_to_numpy)."""
+    import torch
+    assert XT.is_cuda and XT.is_contiguous() and XT.dim() == 2
+    p, ldx = XT.shape
+    n = int(n if n is not None else y.shape[0])
+    xt = LASSO_F32 if XT.dtype == torch.float32 else LASSO_F64
+    if XT.dtype not in (torch.float32, torch.float64):
+        raise TypeError("XT must be float32 or float64")
+    T = int(ratios.shape[0])
+    dev = XT.device
+    opts = opts or lasso_default_opts()
+    words = (p + 31) // 32
+    beta_out = torch.empty((T, p), dtype=torch.float64, device=dev)
+    mask_out = torch.empty((T, words), dtype=torch.int32, device=dev) if want_mask else None
+    stats = torch.empty(T * STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    need = lasso_path_workspace_size(n, p, xt, opts)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    lasso_path(XT.data_ptr(), xt, n, p, ldx, y.data_ptr(), ratios.data_ptr(), T,
+               beta0.data_ptr() if beta0 is not None else None, opts, beta_out.data_ptr(),
+               mask_out.data_ptr() if mask_out is not None else None, stats.data_ptr(),
+               workspace.data_ptr(), workspace.numel(), s.cuda_stream)
+    return dict(beta=beta_out, mask=mask_out, stats=stats, workspace=workspace)

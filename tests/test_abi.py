@@ -1,0 +1,114 @@
+"""The C-ABI boundary without a GPU: the library loads, exports every symbol
+include/lassogs.h declares, and its host-only logic behaves as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1505_03410_gb300.build import build
+    build()
+    import paper_1505_03410_gb300 as p
+    p.load()
+    return p
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lasso_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    lib = ctypes.CDLL(pkg.lassogs.LIB_PATH)
+    declared = _declared_functions()
+    assert set(declared) >= set(pkg.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_default_opts(pkg):
+    o = pkg.lasso_default_opts()
+    assert (o.screen_period, o.dual_point, o.xtr_scope, o.warm_start) == (10, 0, 0, 1)
+    assert o.max_epochs == 100000 and o.gap_tol_rel == 1e-6 and o.gemm_dtype == pkg.LASSO_BF16
+    assert list(o.reserved) == [0, 0, 0]
+
+
+def test_lambda_grid_matches_oracle(pkg):
+    """Sec. 3.3 grid: the library's host helper and the oracle's agree bit for bit."""
+    for T, d in [(100, 3.0), (50, 2.0), (30, 2.0), (1, 3.0), (2, 0.5)]:
+        np.testing.assert_array_equal(pkg.lasso_lambda_grid(T, d), oracle.lambda_ratios(T, d))
+    with pytest.raises(pkg.LassoError) as e:
+        pkg.lasso_lambda_grid(0, 3.0)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError):
+        pkg.lasso_lambda_grid(10, -1.0)
+
+
+def test_workspace_size(pkg):
+    a = pkg.lasso_path_workspace_size(500, 50000, pkg.LASSO_F32)
+    b = pkg.lasso_path_workspace_size(500, 50000, pkg.LASSO_F64)
+    assert 0 < a < b
+    assert pkg.lasso_path_workspace_size(2049, 10, pkg.LASSO_F32) == 0
+    assert pkg.lasso_path_workspace_size(0, 10, pkg.LASSO_F32) == 0
+    assert pkg.lasso_path_workspace_size(10, 0, pkg.LASSO_F32) == 0
+    assert pkg.lasso_path_workspace_size(10, 10, pkg.LASSO_BF16) == 0
+    bad = pkg.lasso_default_opts(screen_period=0)
+    assert pkg.lasso_path_workspace_size(10, 10, pkg.LASSO_F32, bad) == 0
+
+
+def _call(pkg, **kw):
+    args = dict(X=0x10000, x_dtype=pkg.LASSO_F32, n=8, p=16, ldx=8, y=0x20000, lambda_ratios=0x30000, T=4,
+                beta0=None, opts=pkg.lasso_default_opts(), beta_out=0x40000, mask_out=None, stats=0x50000,
+                workspace=0x100000, workspace_bytes=1 << 30, stream=None)
+    args.update(kw)
+    return pkg.lasso_path(**args)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(X=None), 1), (dict(y=None), 1), (dict(stats=None), 1), (dict(n=0), 1), (dict(n=2049), 1),
+    (dict(p=0), 1), (dict(T=0), 1), (dict(ldx=7), 1), (dict(ldx=10), 1), (dict(X=0x10008), 1),
+    (dict(x_dtype=2), 1), (dict(workspace=None), 3), (dict(workspace=0x100010), 3),
+    (dict(workspace_bytes=16), 3),
+])
+def test_argument_errors(pkg, kw, status):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    with pytest.raises(pkg.LassoError) as e:
+        _call(pkg, **kw)
+    assert e.value.status == status
+    assert pkg.lasso_last_error() != ""
+
+
+@pytest.mark.parametrize("field,value", [("screen_period", 0), ("dual_point", 2), ("xtr_scope", -1),
+                                         ("warm_start", 3), ("max_epochs", -1), ("gap_tol_rel", -1.0),
+                                         ("gemm_dtype", 7)])
+def test_option_errors(pkg, field, value):
+    o = pkg.lasso_default_opts(**{field: value})
+    with pytest.raises(pkg.LassoError) as e:
+        _call(pkg, opts=o)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+
+
+def test_product_has_no_cpu_fallback(pkg, tmp_path):
+    """Loading from a path without the library fails loudly."""
+    import importlib
+    mod = importlib.import_module("paper_1505_03410_gb300.lassogs")
+    saved = mod._lib
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError):
+            mod.load(str(tmp_path / "missing.so"))
+    finally:
+        mod._lib = saved

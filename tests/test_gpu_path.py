@@ -1,0 +1,157 @@
+"""GPU path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (from the acceptance rule of the solver): at gap <= tol * ||y||^2
+the objectives agree to 1e-9 relative, coefficients to 1e-5 absolute, and
+supports and safe-active masks are identical.  Both sides run Algorithm 1
+with the same options, so the iterates agree up to rounding; the per-lambda
+pass counts are compared too.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_03410_gb300.build import build
+    build()
+    import paper_1505_03410_gb300 as p
+    return p
+
+
+def run_gpu(pkg, prob, ratios, beta0=None, **opt):
+    dev = torch.device("cuda:0")
+    XT = torch.from_numpy(np.ascontiguousarray(prob["XT"])).to(dev)
+    y = torch.from_numpy(np.ascontiguousarray(prob["y"], dtype=np.float64)).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(ratios, dtype=np.float64)).to(dev)
+    b0 = None if beta0 is None else torch.from_numpy(np.ascontiguousarray(beta0, dtype=np.float64)).to(dev)
+    out = pkg.solve_path(XT, y, r, n=prob["n"], beta0=b0, opts=pkg.lasso_default_opts(**opt))
+    torch.cuda.synchronize()
+    st = pkg.stats_to_numpy(out["stats"])
+    return dict(beta=out["beta"].cpu().numpy(), mask=out["mask"].cpu().numpy().view(np.uint32), stats=st)
+
+
+def run_orc(prob, ratios, beta0=None, **opt):
+    return oracle.lasso_path(prob["XT"], prob["y"], ratios, n=prob["n"], beta0=beta0, **opt)
+
+
+def assert_parity(g, o, check_epochs=True, rtol_obj=1e-9, atol_beta=1e-5):
+    st, so = g["stats"], o["stats"]
+    T = len(st)
+    assert np.all(st["status"] == np.where(so["converged"] == 1, 0, 5)), (st["status"], so["converged"])
+    # lambda_max is a sum of n products: the two sides round it differently
+    np.testing.assert_allclose(st["lambda"], so["lambda"], rtol=1e-12)
+    np.testing.assert_allclose(st["primal"], so["primal"], rtol=rtol_obj)
+    np.testing.assert_allclose(g["beta"], o["beta"], atol=atol_beta, rtol=0)
+    np.testing.assert_array_equal(g["beta"] != 0, o["beta"] != 0)
+    np.testing.assert_array_equal(g["mask"], o["mask"])
+    np.testing.assert_array_equal(st["n_active"], so["n_active"].astype(np.int64))
+    np.testing.assert_array_equal(st["n_nonzero"], so["n_nonzero"].astype(np.int64))
+    if check_epochs:
+        np.testing.assert_array_equal(st["epochs"], so["epochs"].astype(np.int64))
+        np.testing.assert_array_equal(st["checks"], so["checks"].astype(np.int64))
+    assert T == len(so["lambda"])
+
+
+CASES = [
+    # (seed, n, p, dtype, correlated) -- ragged n and p, several CTA slices
+    (101, 37, 300, np.float64, False),
+    (102, 77, 1537, np.float32, False),
+    (103, 130, 3000, np.float32, True),
+    (104, 64, 5000, np.float64, True),
+    (105, 500, 2500, np.float32, True),
+    (106, 611, 900, np.float32, False),
+    (107, 1100, 1300, np.float32, False),
+    (108, 2048, 700, np.float32, False),
+]
+
+
+@pytest.mark.parametrize("seed,n,p,dtype,corr", CASES)
+def test_path_parity(pkg, seed, n, p, dtype, corr):
+    prob = gen.small_problem(seed, n, p, dtype=dtype, k=max(2, min(n, p) // 20), noise=0.2, correlated=corr)
+    ratios = oracle.lambda_ratios(16, 2.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-9)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-9)
+    assert_parity(g, o)
+
+
+def test_path_parity_workload1(pkg):
+    """The full FP64 workload: Gaussian 100 x 1000, 100-point grid to
+    lambda_max/1000, checks every 10 passes, gap <= 1e-6 ||y||^2."""
+    w = gen.workload1()
+    ratios = oracle.lambda_ratios(w["T"], w["delta"])
+    g = run_gpu(pkg, w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
+    o = run_orc(w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("opt", [dict(dual_point=1), dict(xtr_scope=1), dict(warm_start=0),
+                                 dict(screen_period=1), dict(screen_period=3, dual_point=1, xtr_scope=1)])
+def test_options_parity(pkg, opt):
+    prob = gen.small_problem(110, 90, 1200, dtype=np.float32, k=6, noise=0.2, correlated=True)
+    ratios = oracle.lambda_ratios(12, 2.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-8, **opt)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-8, **opt)
+    assert_parity(g, o)
+
+
+def test_beta0_and_screened_nonzero(pkg):
+    """A warm start with nonzero coefficients on inactive features exercises
+    the removal of screened nonzero coefficients (Remark 3)."""
+    prob = gen.small_problem(111, 60, 800, dtype=np.float64, k=4, noise=0.2)
+    rng = np.random.default_rng(111)
+    beta0 = np.zeros(800)
+    beta0[rng.choice(800, 40, replace=False)] = 1e-3 * rng.standard_normal(40)
+    ratios = np.array([0.5, 0.3, 0.2])
+    g = run_gpu(pkg, prob, ratios, beta0=beta0, gap_tol_rel=1e-10)
+    o = run_orc(prob, ratios, beta0=beta0, gap_tol_rel=1e-10)
+    assert_parity(g, o)
+
+
+def test_not_converged_status(pkg):
+    prob = gen.small_problem(112, 50, 600, dtype=np.float32, k=10, noise=0.1)
+    ratios = oracle.lambda_ratios(6, 3.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-12, max_epochs=3)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-12, max_epochs=3)
+    assert (g["stats"]["status"] == 5).any()
+    assert_parity(g, o)
+
+
+def test_tiny_and_degenerate(pkg):
+    # n = 1, p = 1; p < 32; an all-zero column (screened, never updated)
+    for seed, n, p in [(113, 1, 1), (114, 3, 5), (115, 9, 31), (116, 16, 33)]:
+        prob = gen.small_problem(seed, n, p, dtype=np.float64, k=1, noise=0.1)
+        ratios = oracle.lambda_ratios(5, 1.0)
+        assert_parity(run_gpu(pkg, prob, ratios, gap_tol_rel=1e-10), run_orc(prob, ratios, gap_tol_rel=1e-10))
+    prob = gen.small_problem(117, 20, 70, dtype=np.float32, k=3, noise=0.1)
+    prob["XT"][5] = 0.0
+    ratios = oracle.lambda_ratios(6, 1.5)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-10)
+    assert_parity(g, run_orc(prob, ratios, gap_tol_rel=1e-10))
+    assert np.all(g["beta"][:, 5] == 0)
+
+
+def test_nonfinite_input_reported(pkg):
+    prob = gen.small_problem(118, 20, 40, dtype=np.float32, k=2)
+    prob["XT"][3, 4] = np.nan
+    g = run_gpu(pkg, prob, oracle.lambda_ratios(3, 1.0))
+    assert np.all(g["stats"]["status"] == pkg.LASSO_ERR_NONFINITE)
+
+
+def test_workload2_full_size_prefix(pkg):
+    """Toeplitz 500 x 50000 FP32 at full size: the first 40 lambdas of the
+    100-point grid (the oracle finishes them in seconds) match element by
+    element; the launch configuration is the benchmark's."""
+    w = gen.workload2()
+    ratios = oracle.lambda_ratios(w["T"], w["delta"])[:40]
+    g = run_gpu(pkg, w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
+    o = run_orc(w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
+    assert_parity(g, o)
