@@ -81,6 +81,8 @@ typedef struct lasso_path_stats {
   int64_t checks;    /* GAP SAFE checks run at this lambda */
   int64_t n_active;  /* features kept by the last check (|A|, Eq. (6)) */
   int64_t n_nonzero; /* nonzero coefficients of the returned beta */
+  int64_t x_columns; /* columns of X the method reads at this lambda: the X^T rho scope of
+                        every check plus the safe-active set of every pass (algorithmic work) */
   int32_t converged; /* 1 if gap <= eps was reached */
   int32_t status;    /* lasso_status of this lambda (OK, NOT_CONVERGED, TIMEOUT, NONFINITE) */
 } lasso_path_stats;

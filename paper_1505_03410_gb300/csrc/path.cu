@@ -541,7 +541,8 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         a.rho_h[i] = __ldcg(a.rho0_h + i);
         a.rho_l[i] = __ldcg(a.rho0_l + i);
       }
-    long long epochs = 0, checks = 0;
+    long long epochs = 0, checks = 0, xcols = 0;
+    int scope_n = a.p;  // X^T rho scope of the next check
     GSYNC();
 
     for (;;) {
@@ -637,6 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
       const double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
       const double aa = fabs(alpha);
       ++checks;
+      xcols += scope_n;
       const bool stop = Gap <= vload(ctl->eps);
       const bool cap = epochs >= a.max_epochs;
       {
@@ -753,6 +755,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
           st.checks = checks;
           st.n_active = totk;
           st.n_nonzero = totn;
+          st.x_columns = xcols;
           st.converged = stop ? 1 : 0;
           st.status = stop ? kStatusOK : kStatusNotConverged;
           a.stats[t] = st;
@@ -786,6 +789,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         ctl->s = tots;
         ctl->nzl = totz;
       }
+      scope_n = a.xtr_scope == 0 ? a.p : totk;
       GSYNC();
       PROF(0);
       // ======================= PASSES =======================
@@ -990,6 +994,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
             __syncthreads();
           }
           ++epochs;
+          xcols += q;
           GSYNC();
           PROF(4);
           s = vload(ctl->s);

@@ -50,12 +50,14 @@ class LassoPathStats(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("primal", ctypes.c_double), ("dual", ctypes.c_double),
                 ("gap", ctypes.c_double), ("radius", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("epochs", ctypes.c_int64), ("checks", ctypes.c_int64), ("n_active", ctypes.c_int64),
-                ("n_nonzero", ctypes.c_int64), ("converged", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("n_nonzero", ctypes.c_int64), ("x_columns", ctypes.c_int64), ("converged", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
 
 
 STATS_DTYPE = np.dtype([("lambda", "<f8"), ("primal", "<f8"), ("dual", "<f8"), ("gap", "<f8"),
                         ("radius", "<f8"), ("alpha", "<f8"), ("epochs", "<i8"), ("checks", "<i8"),
-                        ("n_active", "<i8"), ("n_nonzero", "<i8"), ("converged", "<i4"), ("status", "<i4")])
+                        ("n_active", "<i8"), ("n_nonzero", "<i8"), ("x_columns", "<i8"), ("converged", "<i4"),
+                        ("status", "<i4")])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(LassoPathStats)
 
 _lock = threading.Lock()
