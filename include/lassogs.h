@@ -134,6 +134,27 @@ lasso_status lasso_path(const void* X_dev, lasso_dtype x_dtype, int64_t n, int64
                         double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
                         void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* lasso_path without a workspace argument, for callers that cannot allocate
+ * device memory where they solve (inside a stream capture, under a host
+ * application that owns the device heap, or on a hot path that must not
+ * allocate).  The paper has no counterpart: this is a deployment variant of
+ * lasso_path with identical results.
+ *
+ * Scratch comes from one static device array of 32 MiB that the library
+ * holds on every GPU that loads it, until the process exits.  Problems whose
+ * lasso_path_workspace_size exceeds 32 MiB return LASSO_ERR_INVALID_ARG.  The
+ * first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * and should come before any stream capture.  All calls on a device share the
+ * array: calls whose GPU work overlaps race and must be serialised by the
+ * caller.  Each call clears what must start at zero before its kernels run.
+ * No memory is allocated.  Other arguments and the return value are as for
+ * lasso_path. */
+lasso_status lasso_path_static(const void* X_dev, lasso_dtype x_dtype, int64_t n, int64_t p, int64_t ldx,
+                               const double* y_dev, const double* lambda_ratios_dev, int32_t T,
+                               const double* beta0_dev, const lasso_opts* opts,
+                               double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
+                               void* stream);
+
 /* Thread-local description of the last error returned on this thread
  * ("" if none).  The pointer stays valid until the next call on the thread. */
 const char* lasso_last_error(void);

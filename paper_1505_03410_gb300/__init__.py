@@ -8,5 +8,5 @@ binding.  Build the library with ``paper_1505_03410_gb300.build.build()``.
 from .lassogs import (EXPORTED, LASSO_BF16, LASSO_ERR_CUDA, LASSO_ERR_INVALID_ARG,  # noqa: F401
                       LASSO_ERR_NONFINITE, LASSO_ERR_NOT_CONVERGED, LASSO_ERR_TIMEOUT, LASSO_ERR_WORKSPACE,
                       LASSO_F32, LASSO_F64, LASSO_OK, STATS_DTYPE, LassoError, LassoOpts, LassoPathStats,
-                      lasso_default_opts, lasso_lambda_grid, lasso_last_error, lasso_path,
+                      lasso_default_opts, lasso_lambda_grid, lasso_last_error, lasso_path, lasso_path_static,
                       lasso_path_workspace_size, load, solve_path, stats_to_numpy)

@@ -30,7 +30,7 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 
 # every symbol include/lassogs.h declares
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
-            "lasso_last_error")
+            "lasso_last_error", "lasso_path_static")
 
 
 class LassoError(RuntimeError):
@@ -83,6 +83,9 @@ def load(path: str | None = None):
             lib.lasso_path.argtypes = [V, ctypes.c_int, I64, I64, I64, V, V, I32, V, ctypes.POINTER(LassoOpts),
                                        V, V, V, V, SZ, V]
             lib.lasso_path.restype = ctypes.c_int
+            lib.lasso_path_static.argtypes = [V, ctypes.c_int, I64, I64, I64, V, V, I32, V,
+                                              ctypes.POINTER(LassoOpts), V, V, V, V]
+            lib.lasso_path_static.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
             lib.lasso_last_error.restype = ctypes.c_char_p
             _lib = lib
@@ -128,6 +131,19 @@ def lasso_path(X, x_dtype, n, p, ldx, y, lambda_ratios, T, beta0, opts, beta_out
                                     int(T), vp(beta0), ctypes.byref(opts) if opts is not None else None,
                                     vp(beta_out), vp(mask_out), vp(stats), vp(workspace), int(workspace_bytes),
                                     vp(stream)))
+
+
+def lasso_path_static(X, x_dtype, n, p, ldx, y, lambda_ratios, T, beta0, opts, beta_out, mask_out, stats,
+                      stream) -> int:
+    """The workspace-free entry point (scratch in a static 32 MiB device array
+    owned by the library): for callers that cannot allocate device memory.
+    Calls that overlap on the GPU race on that array."""
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    return _check(load().lasso_path_static(vp(X), int(x_dtype), int(n), int(p), int(ldx), vp(y),
+                                           vp(lambda_ratios), int(T), vp(beta0),
+                                           ctypes.byref(opts) if opts is not None else None, vp(beta_out),
+                                           vp(mask_out), vp(stats), vp(stream)))
 
 
 def stats_to_numpy(stats_tensor) -> np.ndarray:
