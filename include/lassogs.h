@@ -134,6 +134,34 @@ lasso_status lasso_path(const void* X_dev, lasso_dtype x_dtype, int64_t n, int64
                         double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
                         void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* Bytes of device workspace lasso_batch needs for these sizes on the current
+ * device (0 when the sizes are invalid); 256-byte alignment required. */
+size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_opts* opts);
+
+/* B independent Lasso paths over one design (Algorithm 1 for each): problem b
+ * uses the rows i of X with row_mask_dev[i + b*ldm] != 0 (all rows when
+ * row_mask_dev is NULL) and the responses Y_dev[i + b*ldy] on those rows --
+ * the row-subsampled replicates of stability selection, or many right-hand
+ * sides.  Each problem has its own lambda_max over its rows and follows the
+ * shared grid lambda_t = lambda_max(b) * ratio_t.
+ *
+ *   X_dev        n x p FP32, column-major, ldx % 4 == 0, 16-byte aligned.
+ *   Y_dev        FP64, column b holds problem b's responses (ldy >= n).
+ *   row_mask_dev uint8 n x B (ldm >= n) or NULL.
+ *   beta_out_dev p x T x B FP64 (problem b's solution at lambda_t in
+ *                column t + b*T), mask_out_dev words x T x B uint32 or NULL,
+ *                stats_dev T x B records (index t + b*T).
+ *   Other arguments as for lasso_path; beta0 is not taken (zero start).
+ *
+ * One persistent launch: each resident CTA takes problems from a queue and
+ * runs a whole path per problem (one CTA per problem), so problems of uneven
+ * size balance across the SMs.  Results equal B calls of lasso_path on the
+ * row-restricted problems, up to rounding. */
+lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* Y_dev, int64_t ldy,
+                         const uint8_t* row_mask_dev, int64_t ldm, int64_t B, const double* lambda_ratios_dev,
+                         int32_t T, const lasso_opts* opts, double* beta_out_dev, uint32_t* mask_out_dev,
+                         lasso_path_stats* stats_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* lasso_path without a workspace argument, for callers that cannot allocate
  * device memory where they solve (inside a stream capture, under a host
  * application that owns the device heap, or on a hot path that must not

@@ -9,4 +9,5 @@ from .lassogs import (EXPORTED, LASSO_BF16, LASSO_ERR_CUDA, LASSO_ERR_INVALID_AR
                       LASSO_ERR_NONFINITE, LASSO_ERR_NOT_CONVERGED, LASSO_ERR_TIMEOUT, LASSO_ERR_WORKSPACE,
                       LASSO_F32, LASSO_F64, LASSO_OK, STATS_DTYPE, LassoError, LassoOpts, LassoPathStats,
                       lasso_default_opts, lasso_lambda_grid, lasso_last_error, lasso_path, lasso_path_static,
-                      lasso_path_workspace_size, load, solve_path, stats_to_numpy)
+                      lasso_path_workspace_size, load, solve_path, stats_to_numpy, lasso_batch,
+                      lasso_batch_workspace_size, solve_batch)

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblassogs.so")
 SOURCES = ["api.cu", "path.cu", "static_scratch.cu"]
-HEADERS = ["dfloat.cuh", "device_util.cuh", "internal.h"]
+HEADERS = ["dfloat.cuh", "device_util.cuh", "cd_common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

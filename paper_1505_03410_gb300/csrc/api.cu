@@ -117,6 +117,42 @@ lasso_status lasso_path(const void* X, lasso_dtype xt, int64_t n, int64_t p, int
                      static_cast<cudaStream_t>(stream));
 }
 
+size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_opts* opts) {
+  lasso_opts o;
+  if (opts) o = *opts;
+  else lasso_default_opts(&o);
+  if (check_opts(o) != LASSO_OK) return 0;
+  return batch_workspace_size(n, p, B);
+}
+
+lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
+                         const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
+                         const lasso_opts* opts, double* beta_out, uint32_t* mask_out, lasso_path_stats* stats,
+                         void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  lasso_opts o;
+  if (opts) o = *opts;
+  else lasso_default_opts(&o);
+  lasso_status st = check_opts(o);
+  if (st != LASSO_OK) return st;
+  if (!X || !Y || !ratios || !beta_out || !stats)
+    return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: X, Y, lambda_ratios, beta_out and stats must be non-NULL");
+  if (n < 1 || n > kMaxRows) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: need 1 <= n <= %lld", (long long)kMaxRows);
+  if (p < 1 || p > (int64_t)INT32_MAX / 4) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: p out of range");
+  if (B < 1 || B > (int64_t)INT32_MAX) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: B out of range");
+  if (T < 1) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: T must be >= 1");
+  if (ldx < n || ldx % 4 != 0 || !aligned(X, 16))
+    return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: X needs ldx >= n, ldx %% 4 == 0 and a 16-byte aligned base");
+  if (ldy < n) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: ldy < n");
+  if (row_mask && ldm < n) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: ldm < n");
+  if (!aligned(Y, 8) || !aligned(ratios, 8) || !aligned(beta_out, 8) || !aligned(stats, 8) ||
+      (mask_out && !aligned(mask_out, 4)))
+    return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: misaligned vector argument");
+  if (!ws || !aligned(ws, 256)) return set_error(LASSO_ERR_WORKSPACE, "lasso_batch: workspace must be non-NULL and 256-byte aligned");
+  return batch_launch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, ratios, T, o, beta_out, mask_out, stats, ws, ws_bytes,
+                      static_cast<cudaStream_t>(stream));
+}
+
 const char* lasso_last_error(void) { return g_msg; }
 
 }  // extern "C"

@@ -29,6 +29,11 @@ __device__ __forceinline__ unsigned ld_volatile_u(const unsigned* p) { return *(
 __device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, unsigned nblocks) {
   __syncthreads();
   __shared__ int s_ok;
+  if (nblocks == 1) {  // a one-CTA group: the block barrier is the whole barrier
+    if (threadIdx.x == 0) s_ok = ld_volatile(err) == 0;
+    __syncthreads();
+    return s_ok != 0;
+  }
   if (threadIdx.x == 0) {
     int ok = 1;
     unsigned my_gen = ld_volatile_u(gen);

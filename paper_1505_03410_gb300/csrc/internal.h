@@ -20,6 +20,12 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
                          double* beta_out, uint32_t* mask_out, lasso_path_stats* stats, void* ws, size_t ws_bytes,
                          cudaStream_t stream);
 
+size_t batch_workspace_size(int64_t n, int64_t p, int64_t B);
+lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
+                          const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
+                          const lasso_opts& o, double* beta_out, uint32_t* mask_out, lasso_path_stats* stats,
+                          void* ws, size_t ws_bytes, cudaStream_t stream);
+
 }  // namespace lassogs
 
 #define CUDA_TRY(call)                                                                                   \

@@ -1,0 +1,116 @@
+"""lasso_batch vs the FP64 oracle: B independent paths over one design, each on
+its own row subset (stability-selection replicates) or its own response
+(multi right-hand side).  Each problem is compared element by element with
+the oracle's path on the gathered rows, with the tolerances of the single
+path (objective 1e-9 relative, beta 1e-5, supports, masks and pass counts)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests.test_gpu_path import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1505_03410_gb300.build import build
+    build()
+    import paper_1505_03410_gb300 as p
+    return p
+
+
+def run_gpu_batch(pkg, XT, n, Y, rmask, ratios, **opt):
+    dev = torch.device("cuda:0")
+    Xd = torch.from_numpy(np.ascontiguousarray(XT, dtype=np.float32)).to(dev)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float64)).to(dev)
+    Md = None if rmask is None else torch.from_numpy(np.ascontiguousarray(rmask, dtype=np.uint8)).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(ratios, dtype=np.float64)).to(dev)
+    out = pkg.solve_batch(Xd, Yd, r, n=n, row_mask=Md, opts=pkg.lasso_default_opts(**opt))
+    torch.cuda.synchronize()
+    B, T = Y.shape[0], len(ratios)
+    st = pkg.stats_to_numpy(out["stats"]).reshape(B, T)
+    return dict(beta=out["beta"].cpu().numpy(), mask=out["mask"].cpu().numpy().view(np.uint32), stats=st)
+
+
+def check_batch(g, o):
+    B = g["beta"].shape[0]
+    for b in range(B):
+        gb = dict(beta=g["beta"][b], mask=g["mask"][b], stats=g["stats"][b])
+        ob = dict(beta=o["beta"][b], mask=o["mask"][b], stats={k: v[b] for k, v in o["stats"].items()})
+        assert_parity(gb, ob)
+
+
+def _subsample_problem(seed, n, p, B, frac_lo=0.4, k=5, correlated=False):
+    prob = gen.small_problem(seed, n, p, dtype=np.float32, k=k, noise=0.2, correlated=correlated)
+    rng = np.random.default_rng(seed)
+    rmask = np.zeros((B, n), dtype=np.uint8)
+    Y = np.empty((B, n))
+    for b in range(B):
+        m = int(rng.integers(max(1, int(frac_lo * n)), n + 1))
+        rmask[b, rng.choice(n, size=m, replace=False)] = 1
+        Y[b] = prob["y"] + 0.05 * rng.standard_normal(n)
+    return prob, Y, rmask
+
+
+@pytest.mark.parametrize("seed,n,p,B,corr", [(201, 120, 900, 7, False), (202, 333, 1500, 5, True),
+                                             (203, 64, 640, 3, False)])
+def test_batch_row_subsets(pkg, seed, n, p, B, corr):
+    prob, Y, rmask = _subsample_problem(seed, n, p, B, correlated=corr)
+    ratios = oracle.lambda_ratios(12, 2.0)
+    opt = dict(gap_tol_rel=1e-9, xtr_scope=1)
+    g = run_gpu_batch(pkg, prob["XT"], n, Y, rmask, ratios, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=n, **opt)
+    check_batch(g, o)
+
+
+def test_batch_multi_rhs_no_mask(pkg):
+    prob = gen.small_problem(204, 90, 1100, dtype=np.float32, k=6)
+    rng = np.random.default_rng(204)
+    B = 6
+    Y = np.stack([prob["y"] * rng.uniform(0.5, 2.0) + 0.3 * rng.standard_normal(90) for _ in range(B)])
+    ratios = oracle.lambda_ratios(10, 2.0)
+    g = run_gpu_batch(pkg, prob["XT"], 90, Y, None, ratios, gap_tol_rel=1e-9)
+    o = oracle.lasso_batch(prob["XT"], Y, ratios, n=90, gap_tol_rel=1e-9)
+    check_batch(g, o)
+
+
+def test_batch_more_problems_than_resident_ctas(pkg):
+    """B larger than the number of resident CTAs: the queue hands out every
+    problem exactly once."""
+    prob, Y, rmask = _subsample_problem(205, 40, 200, 500, k=3)
+    ratios = oracle.lambda_ratios(5, 1.5)
+    g = run_gpu_batch(pkg, prob["XT"], 40, Y, rmask, ratios, gap_tol_rel=1e-9)
+    pick = [0, 1, 151, 152, 303, 304, 305, 499]
+    o = oracle.lasso_batch(prob["XT"], (Y * rmask)[pick], ratios, row_mask=rmask[pick], n=40, gap_tol_rel=1e-9)
+    check_batch(dict(beta=g["beta"][pick], mask=g["mask"][pick], stats=g["stats"][pick]), o)
+    assert np.all(g["stats"]["status"] == 0)
+
+
+def test_batch_bad_problem_is_isolated(pkg):
+    """A problem with a NaN response reports NONFINITE; the others solve."""
+    prob, Y, rmask = _subsample_problem(206, 50, 300, 4)
+    Y[2, int(np.nonzero(rmask[2])[0][0])] = np.nan
+    ratios = oracle.lambda_ratios(4, 1.0)
+    g = run_gpu_batch(pkg, prob["XT"], 50, Y, rmask, ratios, gap_tol_rel=1e-9)
+    assert np.all(g["stats"]["status"][2] == pkg.LASSO_ERR_NONFINITE)
+    keep = [0, 1, 3]
+    o = oracle.lasso_batch(prob["XT"], (Y * rmask)[keep], ratios, row_mask=rmask[keep], n=50, gap_tol_rel=1e-9)
+    check_batch(dict(beta=g["beta"][keep], mask=g["mask"][keep], stats=g["stats"][keep]), o)
+
+
+def test_batch_workload3_full_size_prefix(pkg):
+    """Stability-selection workload at full size (Gaussian 1000 x 20000, row
+    subsets of U{400..1000}) for 4 problems on the first 15 lambdas of the
+    50-point grid to lambda_max/100."""
+    w = gen.workload3(B=4)
+    ratios = oracle.lambda_ratios(w["T"], w["delta"])[:15]
+    opt = dict(gap_tol_rel=w["tol"], xtr_scope=1, screen_period=w["f"])
+    g = run_gpu_batch(pkg, w["XT"], w["n"], w["Y"], w["row_mask"], ratios, **opt)
+    o = oracle.lasso_batch(w["XT"], w["Y"], ratios, row_mask=w["row_mask"], n=w["n"], **opt)
+    check_batch(g, o)
