@@ -162,6 +162,22 @@ lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, 
                          int32_t T, const lasso_opts* opts, double* beta_out_dev, uint32_t* mask_out_dev,
                          lasso_path_stats* stats_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* Batched correlations C = X^T R for B residuals at once -- the first GAP
+ * SAFE check of every problem of a batch is this product (Eq. (8) needs
+ * ||X^T rho_b||_inf, Eq. (7) every |x_j^T rho_b|).  Runs on the tensor cores
+ * (tcgen05, BF16 inputs, FP32 accumulation).
+ *
+ *   X_bf16  n x p BF16, column-major, ldx >= n, ldx % 8 == 0, 16-byte aligned
+ *   R_bf16  n x B BF16, column-major, ldr >= n, ldr % 8 == 0, 16-byte aligned
+ *   C       p x B FP32, column-major, ldc >= p (C[j + b*ldc] = x_j^T r_b)
+ *   workspace  >= 256 bytes, 256-byte aligned; its first int receives a
+ *              device-side error code (0 = none, 6 = a wait timed out)
+ * The products of BF16 values are exact in FP32; the sum of n of them carries
+ * the FP32 rounding of the accumulation.  Asynchronous on stream. */
+lasso_status lasso_correlations_bf16(const void* X_bf16, int64_t n, int64_t p, int64_t ldx, const void* R_bf16,
+                                     int64_t ldr, int64_t B, float* C, int64_t ldc, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
 /* lasso_path without a workspace argument, for callers that cannot allocate
  * device memory where they solve (inside a stream capture, under a host
  * application that owns the device heap, or on a hot path that must not

@@ -26,7 +26,7 @@ __device__ __forceinline__ unsigned ld_volatile_u(const unsigned* p) { return *(
 // Sense-free generation barrier across all CTAs of a cooperative launch.
 // count and gen live in global memory; *err is the shared error word.
 // Returns false if the wait timed out or an error is pending.
-__device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, unsigned nblocks) {
+static __device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, unsigned nblocks) {
   __syncthreads();
   __shared__ int s_ok;
   if (nblocks == 1) {  // a one-CTA group: the block barrier is the whole barrier

@@ -30,7 +30,8 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 
 # every symbol include/lassogs.h declares
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
-            "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch")
+            "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch",
+            "lasso_correlations_bf16")
 
 
 class LassoError(RuntimeError):
@@ -91,6 +92,8 @@ def load(path: str | None = None):
             lib.lasso_batch.argtypes = [V, I64, I64, I64, V, I64, V, I64, I64, V, I32, ctypes.POINTER(LassoOpts),
                                         V, V, V, V, SZ, V]
             lib.lasso_batch.restype = ctypes.c_int
+            lib.lasso_correlations_bf16.argtypes = [V, I64, I64, I64, V, I64, I64, V, I64, V, SZ, V]
+            lib.lasso_correlations_bf16.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
             lib.lasso_last_error.restype = ctypes.c_char_p
             _lib = lib
@@ -195,6 +198,14 @@ def solve_batch(XT, Y, ratios, n=None, row_mask=None, opts=None, workspace=None,
                 mask_out.data_ptr() if mask_out is not None else None, stats.data_ptr(), workspace.data_ptr(),
                 workspace.numel(), s.cuda_stream)
     return dict(beta=beta_out, mask=mask_out, stats=stats, workspace=workspace)
+
+
+def lasso_correlations_bf16(X_bf16, n, p, ldx, R_bf16, ldr, B, C, ldc, workspace, workspace_bytes, stream) -> int:
+    """C = X^T R on the tensor cores (pointers as integers)."""
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    return _check(load().lasso_correlations_bf16(vp(X_bf16), int(n), int(p), int(ldx), vp(R_bf16), int(ldr), int(B),
+                                                 vp(C), int(ldc), vp(workspace), int(workspace_bytes), vp(stream)))
 
 
 def stats_to_numpy(stats_tensor) -> np.ndarray:
