@@ -153,10 +153,19 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
  *                stats_dev T x B records (index t + b*T).
  *   Other arguments as for lasso_path; beta0 is not taken (zero start).
  *
- * One persistent launch: each resident CTA takes problems from a queue and
- * runs a whole path per problem (one CTA per problem), so problems of uneven
- * size balance across the SMs.  Results equal B calls of lasso_path on the
- * row-restricted problems, up to rounding. */
+ * opts->gemm_dtype selects how the first check of every lambda gets X^T rho:
+ *   LASSO_F32   one persistent launch; each resident CTA takes problems from
+ *               a queue and runs a whole path per problem with FP32 CUDA-core
+ *               passes (workspace: one region per resident CTA);
+ *   LASSO_BF16  lockstep over lambda (default): per lambda one tensor-core
+ *               product C = X^T R for all problems in split BF16 (x ~ xh + xl,
+ *               r ~ rh + rl, three BF16 GEMM terms, FP32 accumulation, error
+ *               <= (3 2^-16 + 2^-20 + 3L 2^-24) |x||r|, L = n rounded up to 8),
+ *               then one launch that advances every problem by one lambda
+ *               (workspace: one region per problem plus the packed operands).
+ * Either way the test decisions equal the exact ones: features the error
+ * bound leaves undecided are recomputed exactly.  Results equal B calls of
+ * lasso_path on the row-restricted problems, up to rounding. */
 lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* Y_dev, int64_t ldy,
                          const uint8_t* row_mask_dev, int64_t ldm, int64_t B, const double* lambda_ratios_dev,
                          int32_t T, const lasso_opts* opts, double* beta_out_dev, uint32_t* mask_out_dev,

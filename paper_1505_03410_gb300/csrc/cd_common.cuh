@@ -204,7 +204,7 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
     ChainRec r;
     r.tab = __ldcg(a.ftab + j);
     r.b = ld_beta(a, j);
-    r.nf = __ldg(a.nrmf + j);
+    r.nf = __ldcg(a.nrmf + j);
     r.j = j;
     a.recs[c] = r;
     jl[c] = j;

@@ -29,6 +29,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include "cd_common.cuh"
 #include "internal.h"
 
@@ -47,7 +49,7 @@ struct Ctrl {
   int q, s;                   // safe-active and support counts
   int pos, round_end, nc, done, sup_idx, forced, n_entered;
   float rho_bound;            // bound on ||rho|| for every snapshot of a round
-  int pad0;
+  int failed;                 // lockstep batches: error code of a problem that failed earlier
   // cycle counters of CTA 0 by phase (check, chain, verify, rollback/accept,
   // end of pass, setup of a round) and event counts (rounds, rollbacks)
   unsigned long long prof[8];
@@ -83,6 +85,13 @@ struct Args {
   const uint8_t* rmask;
   int* queue;       // next problem to take
   double tol;       // gap_tol_rel
+  // lockstep batches: one launch per lambda range [t0, t1), workspace region
+  // per problem (not per CTA), and the first check of each lambda reads
+  // cfirst[j + b * ldc] with the forward-error factor cfactor
+  int lockstep, t0, t1;
+  const float* cfirst;
+  long long ldc;
+  float cfactor;
 };
 
 // Fields the shared helpers read (see cd_common.cuh), built from a CTA's
@@ -221,13 +230,13 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
   __shared__ float fbuf[32];
   __shared__ int s_prob;
 
-  char* const wsb = a.ws + (BATCH ? (size_t)blockIdx.x * a.cta_bytes : (size_t)0);
+  char* wsb = a.ws + (BATCH ? (size_t)blockIdx.x * a.cta_bytes : (size_t)0);
 #define WS(T, name) reinterpret_cast<T*>(wsb + a.o_##name)
   Ctrl* ctl = WS(Ctrl, ctrl);
   const int cta = BATCH ? 0 : (int)blockIdx.x, G = BATCH ? 1 : (int)gridDim.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = kThreads / 32;
   const int f0 = BATCH ? 0 : slice_begin(a, cta), f1 = BATCH ? a.p : slice_begin(a, cta + 1);
-  const ChainCtx cx{a.Xh,          a.Xl,           a.ldx,           a.ldw,          a.n,
+  ChainCtx cx{a.Xh,          a.Xl,           a.ldx,           a.ldw,          a.n,
                     a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
                     WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap)};
   // dynamic shared memory of CTA 0: feature list of a round, then the column ring
@@ -238,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
   int* err = &ctl->err;
   const double u64 = 1.1102230246251565e-16;  // 2^-53
   const float bf = fp32_bound_factor<NG, XLO>();
+  float bfc = bf;  // bound factor of the current check's c~
   float4 rh[NGC], rl[NGC];  // chain registers (CTA 0)
   long long tprof = clock64();
   const bool prof_thread = !BATCH && blockIdx.x == 0 && tid == 0;
@@ -263,7 +273,26 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
       b = s_prob;
       __syncthreads();
       if (b >= a.B) break;
-      batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+      if (a.lockstep) {
+        // this problem's own region carries its state from launch to launch
+        wsb = a.ws + (size_t)b * a.cta_bytes;
+        ctl = WS(Ctrl, ctrl);
+        bc = &ctl->bar_count;
+        bg = &ctl->bar_gen;
+        err = &ctl->err;
+        cx = ChainCtx{a.Xh,          a.Xl,           a.ldx,           a.ldw,            a.n,
+                      a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
+                      WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap)};
+        if (a.t0 == 0) {
+          batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+          if (tid == 0) ctl->failed = 0;
+          __syncthreads();
+        } else if (vload(ctl->failed) != 0) {
+          continue;  // its records were stamped when it failed
+        }
+      } else {
+        batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+      }
     } else if (it > 0) {
       break;
     }
@@ -275,7 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
     const uint32_t rbits = BATCH ? chain_row_bits<NGC>(a, b) : 0xffffffffu;
     if (vload(*err) != 0) goto fail;  // NaN/Inf input or lambda_max = 0
 
-  for (int t = 0; t < a.T; ++t) {
+  const int t_begin = (BATCH && a.lockstep) ? a.t0 : 0, t_end = (BATCH && a.lockstep) ? a.t1 : a.T;
+  for (int t = t_begin; t < t_end; ++t) {
     const double lam = __dmul_rn(vload(ctl->lambda_max), a.ratios[t]);
     // per-lambda table lambda / ||x_j||^2; full mask; optional restart
     for (int j = f0 + tid; j < f1; j += kThreads) {
@@ -320,12 +350,17 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
           r4[k] = (g < a.ld4) ? ldcg4(WS(float, rho_h), g) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float mlo = 0.f;
+        // the first check of a lambda of a lockstep batch takes c~ from the
+        // batched tensor-core product, with its own error factor
+        const bool from_gemm = BATCH && a.cfirst != nullptr && checks == 0;
+        bfc = from_gemm ? a.cfactor : bf;
         for (int j = f0 + warp; j < f1; j += nwarps) {
           const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
           float c = 0.f;
           if (in) {
-            c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-            const float E = __fmul_ru(__fmul_ru(bf, __ldg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
+            c = from_gemm ? __ldcg(a.cfirst + (size_t)j + (size_t)b * a.ldc)
+                          : warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
+            const float E = __fmul_ru(__fmul_ru(bfc, __ldcg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
             mlo = fmaxf(mlo, __fsub_rd(fabsf(c), E));
           }
           if (lane == 0) WS(float, ctil)[j] = c;
@@ -347,8 +382,8 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
           const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
           if (!in) continue;
           const float c = __ldcg(WS(float, ctil) + j);
-          const float nf = __ldg(WS(float, nrmf) + j);
-          const float E = __fmul_ru(__fmul_ru(bf, nf), rnormf) + 1e-37f;
+          const float nf = __ldcg(WS(float, nrmf) + j);
+          const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
           if (__fadd_ru(fabsf(c), E) >= mlo) {
             const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l), __fmul_ru(nf, rnormf));
             const double cv = fabs(df_to_double(ce));
@@ -408,11 +443,11 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
           bool keep = was, amb = false;
           if (was) {
             const float c = __ldcg(WS(float, ctil) + j);
-            const float nf = __ldg(WS(float, nrmf) + j);
-            const float E = __fmul_ru(__fmul_ru(bf, nf), rnormf) + 1e-37f;
+            const float nf = __ldcg(WS(float, nrmf) + j);
+            const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
             // rigorous FP32 brackets of mu_j = |c_j| |alpha| + r ||x_j||
             const float mu_hi = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(c), E), aaf_hi), __fmul_ru(radf_hi, nf));
-            const float nfl = __double2float_rd(__ldg(WS(double, nrm) + j));
+            const float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
             const float clo = fmaxf(__fsub_rd(fabsf(c), E), 0.f);
             const float mu_lo = __fadd_rd(__fmul_rd(clo, aaf_lo), __fmul_rd(radf_lo, nfl));
             if (mu_hi < 0.999999f) keep = false;
@@ -425,8 +460,8 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
             const int l = __ffs(ambm) - 1;
             ambm &= ambm - 1;
             const int jj = w0 + l;
-            const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldg(WS(float, nrmf) + jj), rnormf));
-            const double mu = __dadd_rn(__dmul_rn(fabs(df_to_double(ce)), aa), __dmul_rn(rad, __ldg(WS(double, nrm) + jj)));
+            const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldcg(WS(float, nrmf) + jj), rnormf));
+            const double mu = __dadd_rn(__dmul_rn(fabs(df_to_double(ce)), aa), __dmul_rn(rad, __ldcg(WS(double, nrm) + jj)));
             if (lane == l) keep = !(mu < 1.0);
           }
           const float2 bj = valid ? ld_beta(cx, j) : make_float2(0.f, 0.f);
@@ -657,7 +692,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
                   }
                   const int j = __ldcg(WS(int, A) + i);
                   const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-                  const float nf = __ldg(WS(float, nrmf) + j);
+                  const float nf = __ldcg(WS(float, nrmf) + j);
                   const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
                   bool enters;
                   if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
@@ -771,15 +806,20 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
     {
       const int e = vload(*err);
       lasso_path_stats* so = a.stats + (size_t)b * a.T;
-      for (int t = tid; t < a.T; t += kThreads) {
+      const int tf0 = a.lockstep ? a.t0 : 0;
+      for (int t = tf0 + tid; t < a.T; t += kThreads) {
         lasso_path_stats st{};
         st.lambda = vload(ctl->lambda_max) * a.ratios[t];
         st.status = e;
         so[t] = st;
       }
-      for (size_t k = tid; k < (size_t)a.T * a.p; k += kThreads) a.beta_out[(size_t)b * a.T * a.p + k] = 0.0;
+      for (size_t k = (size_t)tf0 * a.p + tid; k < (size_t)a.T * a.p; k += kThreads)
+        a.beta_out[(size_t)b * a.T * a.p + k] = 0.0;
       __syncthreads();
-      if (tid == 0) ctl->err = 0;
+      if (tid == 0) {
+        ctl->err = 0;
+        ctl->failed = e;
+      }
       __syncthreads();
     }
   }
@@ -891,6 +931,61 @@ __global__ void stats_error_kernel(Ctrl* ctl, lasso_path_stats* stats, int T) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
     stats[t].status = e;
     stats[t].converged = 0;
+  }
+}
+
+// ---------------------------------------------------------------- split-BF16 operands
+// A value v (FP32) is carried as vh = bf16(v) and vl = bf16(v - vh), so that
+// |v - vh - vl| <= 2^-16 |v|.  The three products that matter,
+//   x.r ~ xh.rh + xh.rl + xl.rh   (the dropped xl.rl is <= 2^-16 |x r|),
+// are one GEMM over a K dimension of 3 L: the design row j is packed as
+// [xh | xh | xl] and the residual of problem b as [rh | rl | rh] (L = n
+// rounded up to 8, zero padded).  Every product of two BF16 values is exact
+// in FP32, so the error of c~ is at most (3 2^-16 + 2^-20) |x||r| plus the
+// FP32 accumulation of 3 L terms.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+}
+
+__global__ void pack_x_kernel(const float* __restrict__ X, long long ldx, int n, int p, int L,
+                              __nv_bfloat16* __restrict__ X3) {
+  const long long total = (long long)p * L;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / L), i = (int)(k % L);
+    const float v = i < n ? X[(long long)j * ldx + i] : 0.f;
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    __nv_bfloat16* row = X3 + (long long)j * 3 * L;
+    row[i] = h;
+    row[L + i] = h;
+    row[2 * L + i] = l;
+  }
+}
+
+// residuals of the B problems: from the masked responses (first lambda) or
+// from the FP32 high planes of the residuals kept in each problem's region
+__global__ void pack_r_kernel(const double* Y, long long ldy, const uint8_t* rmask, long long ldm, const char* ws,
+                              size_t region, size_t o_rho_h, int n, int B, int L, int from_y,
+                              __nv_bfloat16* __restrict__ R3) {
+  const long long total = (long long)B * L;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(k / L), i = (int)(k % L);
+    float v = 0.f;
+    if (i < n) {
+      if (from_y) {
+        const bool in = rmask == nullptr || rmask[i + (size_t)b * ldm] != 0;
+        v = in ? (float)Y[i + (size_t)b * ldy] : 0.f;
+      } else {
+        v = reinterpret_cast<const float*>(ws + (size_t)b * region + o_rho_h)[i];
+      }
+    }
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    __nv_bfloat16* row = R3 + (long long)b * 3 * L;
+    row[i] = h;
+    row[L + i] = l;
+    row[2 * L + i] = h;
   }
 }
 
@@ -1150,13 +1245,50 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
 }
 
 // ---------------------------------------------------------------- batched
-size_t batch_workspace_size(int64_t n, int64_t p, int64_t B) {
-  if (n < 1 || n > kMaxRows || p < 1 || p > (int64_t)INT32_MAX / 4 || B < 1) return 0;
+namespace {
+struct BatchLayout {
+  Layout L;
+  int grid, regions;
+  bool lockstep;
+  long long Lk;  // K segment length of the split-BF16 operands
+  size_t o_regions, o_x3, o_r3, o_c, o_gerr, total;
+};
+
+BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms) {
+  BatchLayout bl{};
+  bl.L = make_layout(n, p, kSCapBatch, false);
+  bl.grid = batch_grid(B, sms);
+  bl.lockstep = lockstep;
+  bl.regions = lockstep ? (int)B : bl.grid;
+  bl.Lk = (n + 7) / 8 * 8;
+  size_t off = 256;
+  bl.o_regions = off;
+  off += bl.L.region * (size_t)bl.regions;
+  if (lockstep) {
+    bl.o_x3 = off;
+    off += align256(sizeof(__nv_bfloat16) * 3 * (size_t)bl.Lk * (size_t)p);
+    bl.o_r3 = off;
+    off += align256(sizeof(__nv_bfloat16) * 3 * (size_t)bl.Lk * (size_t)B);
+    bl.o_c = off;
+    off += align256(sizeof(float) * (size_t)p * (size_t)B);
+    bl.o_gerr = off;
+    off += 256;
+  }
+  bl.total = off;
+  return bl;
+}
+
+int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     sms = 152;
-  const Layout L = make_layout(n, p, kSCapBatch, false);
-  return 256 + L.region * (size_t)batch_grid(B, sms);
+  return sms;
+}
+}  // namespace
+
+size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep) {
+  if (n < 1 || n > kMaxRows || p < 1 || p > (int64_t)INT32_MAX / 4 || B < 1) return 0;
+  return batch_layout(n, p, B, lockstep, device_sms()).total;
 }
 
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
@@ -1166,18 +1298,17 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   DevInfo d{};
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
-  const Layout L = make_layout(n, p, kSCapBatch, false);
-  const int grid = batch_grid(B, d.sms);
-  const size_t need = 256 + L.region * (size_t)grid;
-  if (ws_bytes < need)
+  const bool lockstep = o.gemm_dtype == LASSO_BF16;
+  const BatchLayout bl = batch_layout(n, p, B, lockstep, d.sms);
+  if (ws_bytes < bl.total)
     return set_error(LASSO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes required", ws_bytes,
-                     need);
+                     bl.total);
   char* base = static_cast<char*>(ws);
   Args a{};
   fill_common(a, n, p, T, o);
-  set_offsets(a, L);
-  a.ws = base + 256;
-  a.cta_bytes = L.region;
+  set_offsets(a, bl.L);
+  a.ws = base + bl.o_regions;
+  a.cta_bytes = bl.L.region;
   a.B = (int)B;
   a.y = Y;
   a.ldy = ldy;
@@ -1194,15 +1325,44 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   a.fs = (int)((p + 31) / 32 * 32);
   const int ngc = ngc_for(n);
   const void* kfn = pick_kernel(ngc, false, true);
-  const size_t dyn = dyn_smem(L.s_cap, ngc, false);
+  const size_t dyn = dyn_smem(bl.L.s_cap, ngc, false);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
   CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  // the problem queue starts at 0; each CTA clears its control block when it
-  // takes a problem (batch_setup)
-  CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
-  void* params[] = {&a};
-  CUDA_TRY(cudaLaunchKernel(kfn, dim3(grid), dim3(kThreads), params, dyn, stream));
+  if (!lockstep) {
+    // each CTA solves whole paths; its first checks are CUDA-core FP32 passes
+    CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
+    void* params[] = {&a};
+    CUDA_TRY(cudaLaunchKernel(kfn, dim3(bl.grid), dim3(kThreads), params, dyn, stream));
+    return LASSO_OK;
+  }
+  // lockstep: per lambda, the residuals of all problems -> one tensor-core
+  // product C = X^T R (split BF16) -> one launch that advances every problem
+  // by one lambda, its first check reading C with the split-BF16 error factor
+  const long long Lk = bl.Lk;
+  __nv_bfloat16* X3 = reinterpret_cast<__nv_bfloat16*>(base + bl.o_x3);
+  __nv_bfloat16* R3 = reinterpret_cast<__nv_bfloat16*>(base + bl.o_r3);
+  float* C = reinterpret_cast<float*>(base + bl.o_c);
+  int* gerr = reinterpret_cast<int*>(base + bl.o_gerr);
+  a.lockstep = 1;
+  a.cfirst = C;
+  a.ldc = p;
+  a.cfactor = (float)((3.0 * 0x1p-16 + 0x1p-20 + (3.0 * (double)Lk + 8.0) * 0x1p-24) * 1.05);
+  CUDA_TRY(cudaMemsetAsync(gerr, 0, 256, stream));
+  pack_x_kernel<<<d.sms * 8, 256, 0, stream>>>(X, ldx, (int)n, (int)p, (int)Lk, X3);
+  CUDA_TRY(cudaGetLastError());
+  for (int t = 0; t < T; ++t) {
+    pack_r_kernel<<<d.sms * 4, 256, 0, stream>>>(Y, ldy, row_mask, ldm, a.ws, a.cta_bytes, a.o_rho_h, (int)n, (int)B,
+                                                 (int)Lk, t == 0 ? 1 : 0, R3);
+    CUDA_TRY(cudaGetLastError());
+    st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream);
+    if (st != LASSO_OK) return st;
+    CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
+    a.t0 = t;
+    a.t1 = t + 1;
+    void* params[] = {&a};
+    CUDA_TRY(cudaLaunchKernel(kfn, dim3(bl.grid), dim3(kThreads), params, dyn, stream));
+  }
   return LASSO_OK;
 }
 

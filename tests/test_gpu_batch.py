@@ -58,59 +58,70 @@ def _subsample_problem(seed, n, p, B, frac_lo=0.4, k=5, correlated=False):
     return prob, Y, rmask
 
 
+# gemm_dtype 1 (LASSO_F32): every CTA runs whole paths, its checks are FP32
+# CUDA-core passes; 2 (LASSO_BF16): lockstep over lambda, the first check of
+# every lambda comes from one split-BF16 tensor-core product for all problems
+GEMM = [1, 2]
+
+
+@pytest.mark.parametrize("gemm", GEMM)
 @pytest.mark.parametrize("seed,n,p,B,corr", [(201, 120, 900, 7, False), (202, 333, 1500, 5, True),
                                              (203, 64, 640, 3, False)])
-def test_batch_row_subsets(pkg, seed, n, p, B, corr):
+def test_batch_row_subsets(pkg, seed, n, p, B, corr, gemm):
     prob, Y, rmask = _subsample_problem(seed, n, p, B, correlated=corr)
     ratios = oracle.lambda_ratios(12, 2.0)
     opt = dict(gap_tol_rel=1e-9, xtr_scope=1)
-    g = run_gpu_batch(pkg, prob["XT"], n, Y, rmask, ratios, **opt)
+    g = run_gpu_batch(pkg, prob["XT"], n, Y, rmask, ratios, gemm_dtype=gemm, **opt)
     o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=n, **opt)
     check_batch(g, o)
 
 
-def test_batch_multi_rhs_no_mask(pkg):
+@pytest.mark.parametrize("gemm", GEMM)
+def test_batch_multi_rhs_no_mask(pkg, gemm):
     prob = gen.small_problem(204, 90, 1100, dtype=np.float32, k=6)
     rng = np.random.default_rng(204)
     B = 6
     Y = np.stack([prob["y"] * rng.uniform(0.5, 2.0) + 0.3 * rng.standard_normal(90) for _ in range(B)])
     ratios = oracle.lambda_ratios(10, 2.0)
-    g = run_gpu_batch(pkg, prob["XT"], 90, Y, None, ratios, gap_tol_rel=1e-9)
+    g = run_gpu_batch(pkg, prob["XT"], 90, Y, None, ratios, gap_tol_rel=1e-9, gemm_dtype=gemm)
     o = oracle.lasso_batch(prob["XT"], Y, ratios, n=90, gap_tol_rel=1e-9)
     check_batch(g, o)
 
 
-def test_batch_more_problems_than_resident_ctas(pkg):
+@pytest.mark.parametrize("gemm", GEMM)
+def test_batch_more_problems_than_resident_ctas(pkg, gemm):
     """B larger than the number of resident CTAs: the queue hands out every
     problem exactly once."""
     prob, Y, rmask = _subsample_problem(205, 40, 200, 500, k=3)
     ratios = oracle.lambda_ratios(5, 1.5)
-    g = run_gpu_batch(pkg, prob["XT"], 40, Y, rmask, ratios, gap_tol_rel=1e-9)
+    g = run_gpu_batch(pkg, prob["XT"], 40, Y, rmask, ratios, gap_tol_rel=1e-9, gemm_dtype=gemm)
     pick = [0, 1, 151, 152, 303, 304, 305, 499]
     o = oracle.lasso_batch(prob["XT"], (Y * rmask)[pick], ratios, row_mask=rmask[pick], n=40, gap_tol_rel=1e-9)
     check_batch(dict(beta=g["beta"][pick], mask=g["mask"][pick], stats=g["stats"][pick]), o)
     assert np.all(g["stats"]["status"] == 0)
 
 
-def test_batch_bad_problem_is_isolated(pkg):
+@pytest.mark.parametrize("gemm", GEMM)
+def test_batch_bad_problem_is_isolated(pkg, gemm):
     """A problem with a NaN response reports NONFINITE; the others solve."""
     prob, Y, rmask = _subsample_problem(206, 50, 300, 4)
     Y[2, int(np.nonzero(rmask[2])[0][0])] = np.nan
     ratios = oracle.lambda_ratios(4, 1.0)
-    g = run_gpu_batch(pkg, prob["XT"], 50, Y, rmask, ratios, gap_tol_rel=1e-9)
+    g = run_gpu_batch(pkg, prob["XT"], 50, Y, rmask, ratios, gap_tol_rel=1e-9, gemm_dtype=gemm)
     assert np.all(g["stats"]["status"][2] == pkg.LASSO_ERR_NONFINITE)
     keep = [0, 1, 3]
     o = oracle.lasso_batch(prob["XT"], (Y * rmask)[keep], ratios, row_mask=rmask[keep], n=50, gap_tol_rel=1e-9)
     check_batch(dict(beta=g["beta"][keep], mask=g["mask"][keep], stats=g["stats"][keep]), o)
 
 
-def test_batch_workload3_full_size_prefix(pkg):
+@pytest.mark.parametrize("gemm", GEMM)
+def test_batch_workload3_full_size_prefix(pkg, gemm):
     """Stability-selection workload at full size (Gaussian 1000 x 20000, row
     subsets of U{400..1000}) for 4 problems on the first 15 lambdas of the
     50-point grid to lambda_max/100."""
     w = gen.workload3(B=4)
     ratios = oracle.lambda_ratios(w["T"], w["delta"])[:15]
     opt = dict(gap_tol_rel=w["tol"], xtr_scope=1, screen_period=w["f"])
-    g = run_gpu_batch(pkg, w["XT"], w["n"], w["Y"], w["row_mask"], ratios, **opt)
+    g = run_gpu_batch(pkg, w["XT"], w["n"], w["Y"], w["row_mask"], ratios, gemm_dtype=gemm, **opt)
     o = oracle.lasso_batch(w["XT"], w["Y"], ratios, row_mask=w["row_mask"], n=w["n"], **opt)
     check_batch(g, o)
