@@ -3,7 +3,7 @@
 // with limb reduction), the soft-threshold step of Algorithm 1, and the
 // coordinate chain (sequential updates of the nonzero coefficients with
 // cp.async-staged columns).  Functions taking a context `a` need its fields
-// Xh, Xl, ldx, ld4, n, ldw, A, chain, ftab, bdf, nrmf, recs, oldb, snap.
+// Xh, Xl, ldx, ld4, n, ldw, A, chain, ftab, bdf, nrmf, recs, oldb, snap, msnap.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -219,6 +219,8 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
     }
     ChainRec r0 = a.recs[0];
     ChainRec r1 = (nc > 1) ? a.recs[1] : r0;
+    // movement bound sum |delta| ||x_j|| (thread 0): snapshot e + 1 carries it
+    float mv = (tid == 0) ? a.msnap[0] : 0.f;
     for (int e = 0; e < nc; ++e) {
       const int slot = e % kRing;
       cp_async_wait<kRing - 1>();  // this thread's copies for entry e have landed
@@ -268,6 +270,8 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
       if (tid == 0) {
         a.oldb[e] = r0.b;
         a.bdf[r0.j] = make_float2(nb.h, nb.l);
+        mv = __fadd_ru(mv, __fmul_ru(__fadd_ru(fabsf(d.h), fabsf(d.l)), r0.nf));
+        a.msnap[e + 1] = mv;
       }
       if (!df_is_zero(d)) {
 #pragma unroll

@@ -36,6 +36,10 @@
 
 namespace lassogs {
 
+// certificate values of a position: a chain entry (never verified), or a zero
+// coefficient without a valid certificate (always verified)
+constexpr float kSkChain = 3.0e38f;
+constexpr float kSkNone = -3.0e38f;
 
 struct Ctrl {
   unsigned bar_count, bar_gen;
@@ -50,6 +54,7 @@ struct Ctrl {
   int pos, round_end, nc, done, sup_idx, forced, n_entered;
   float rho_bound;            // bound on ||rho|| for every snapshot of a round
   int failed;                 // lockstep batches: error code of a problem that failed earlier
+  float mcur;                 // movement bound: sum |delta_c| ||x_c|| since the last check (rounded up)
   // cycle counters of CTA 0 by phase (check, chain, verify, rollback/accept,
   // end of pass, setup of a round) and event counts (rounds, rollbacks)
   unsigned long long prof[8];
@@ -77,7 +82,7 @@ struct Args {
   size_t cta_bytes;
   size_t o_ctrl, o_cnt_kept, o_cnt_sup, o_cnt_nnz, o_cnt_zero, o_part_l1, o_nrm, o_nrmf, o_ftab, o_bdf, o_b0df,
       o_rho_h, o_rho_l, o_rho0_h, o_rho0_l, o_ctil, o_mask, o_A, o_sup0, o_sup1, o_chain, o_entered, o_oldb, o_recs,
-      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb;
+      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb, o_sk, o_mref, o_msnap;
   // batched solver: B problems over the same X, problem b uses column b of Y
   // (ld ldy) and the rows i with rmask[i + b * ldm] != 0 (all rows if null)
   int B;
@@ -109,6 +114,7 @@ struct ChainCtx {
   ChainRec* recs;
   float2* oldb;
   float* snap;
+  float* msnap;
 };
 
 __device__ __forceinline__ int slice_begin(const Args& a, int c) {
@@ -221,7 +227,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
 // BATCH = true: every CTA is a one-CTA "grid" with its own workspace copy and
 // solves problems taken from a queue, one whole path at a time.
 template <int NGC, bool XLO, bool BATCH>
-__global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
+__global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
   constexpr int NG = 4 * NGC;  // float4 granules per lane in warp-wide dots
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ ChainSmem cs;
@@ -236,9 +242,12 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
   const int cta = BATCH ? 0 : (int)blockIdx.x, G = BATCH ? 1 : (int)gridDim.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = kThreads / 32;
   const int f0 = BATCH ? 0 : slice_begin(a, cta), f1 = BATCH ? a.p : slice_begin(a, cta + 1);
+  // mask words of the slice: f0 is a multiple of 32 when the slice is not
+  // empty; CTAs past the last feature (f0 == f1 == p) own no word
+  const int wd0 = f0 >> 5, wd1 = f1 > f0 ? (f1 + 31) >> 5 : wd0;
   ChainCtx cx{a.Xh,          a.Xl,           a.ldx,           a.ldw,          a.n,
                     a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
-                    WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap)};
+                    WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap), WS(float, msnap)};
   // dynamic shared memory of CTA 0: feature list of a round, then the column ring
   int* jl = reinterpret_cast<int*>(dsm);
   float4* ring = reinterpret_cast<float4*>(dsm + (((size_t)(a.s_cap + 1) * sizeof(int) + 127) & ~(size_t)127));
@@ -250,7 +259,9 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
   float bfc = bf;  // bound factor of the current check's c~
   float4 rh[NGC], rl[NGC];  // chain registers (CTA 0)
   long long tprof = clock64();
-  const bool prof_thread = !BATCH && blockIdx.x == 0 && tid == 0;
+  // phase counters: thread 0 of CTA 0 (single path) or of every CTA (batched,
+  // the counters of the problem it solved last)
+  const bool prof_thread = BATCH ? tid == 0 : (blockIdx.x == 0 && tid == 0);
 #define PROF(k)                                   \
   do {                                            \
     if (prof_thread) {                            \
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         err = &ctl->err;
         cx = ChainCtx{a.Xh,          a.Xl,           a.ldx,           a.ldw,            a.n,
                       a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
-                      WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap)};
+                      WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap), WS(float, msnap)};
         if (a.t0 == 0) {
           batch_setup<XLO>(a, ctl, wsb, b, dbuf);
           if (tid == 0) ctl->failed = 0;
@@ -292,6 +303,10 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         }
       } else {
         batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+      }
+      if (prof_thread && (!a.lockstep || a.t0 == 0)) {
+        for (int k = 0; k < 8; ++k) ctl->prof[k] = 0ull;
+        tprof = clock64();
       }
     } else if (it > 0) {
       break;
@@ -316,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
       WS(float4, ftab)[j] = tb;
       if (t > 0 && !a.warm_start) WS(float2, bdf)[j] = WS(float2, b0df)[j];
     }
-    for (int w = f0 / 32 + tid; w < (f1 + 31) / 32; w += kThreads) {
+    for (int w = wd0 + tid; w < wd1; w += kThreads) {
       const int lo = w * 32, hi = min(a.p, lo + 32);
       WS(uint32_t, mask)[w] = (hi - lo == 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
     }
@@ -530,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
           bout[(long long)t * a.p + j] = __dadd_rn((double)b.x, (double)b.y);
         }
         if (mout)
-          for (int w = f0 / 32 + tid; w < (f1 + 31) / 32; w += kThreads)
+          for (int w = wd0 + tid; w < wd1; w += kThreads)
             mout[(long long)t * a.words + w] = __ldcg(WS(uint32_t, mask) + w);
         if (cta == 0 && tid == 0) {
           lasso_path_stats st;
@@ -553,19 +568,62 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         break;
       }
       // compaction: ascending safe-active list A, support positions sup0 and
-      // the ascending list of coefficients the check set to zero
-      if (warp == 0) {
+      // the ascending list of coefficients the check set to zero.  Each warp
+      // takes a contiguous run of the slice's mask words: count, prefix over
+      // the warps, write.
+      {
+        const int w_first = wd0, w_last = wd1;
+        const int nwd = w_last - w_first, per = (nwd + nwarps - 1) / nwarps;
+        const int wb = w_first + warp * per, we = min(w_last, wb + per);
+        int ck = 0, cs_ = 0, cz = 0;
+        for (int w = wb; w < we; ++w) {
+          const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
+          const int j = w * 32 + lane;
+          const bool keep = (word >> lane) & 1u;
+          const bool nz = keep && nonzero2(ld_beta(cx, j));
+          ck += __popc(word);
+          cs_ += __popc(__ballot_sync(0xffffffffu, nz));
+          cz += __popc(__ldcg(WS(uint32_t, zbits) + w));
+        }
+        __syncthreads();
+        if (lane == 0) {
+          ibuf[warp] = ck;
+          ibuf[8 + warp] = cs_;
+          ibuf[16 + warp] = cz;
+        }
+        __syncthreads();
         int runk = pk, runs = ps, runz = pz;
-        for (int w0 = f0; w0 < f1; w0 += 32) {
-          const int j = w0 + lane;
-          const uint32_t word = __ldcg(WS(uint32_t, mask) + (w0 >> 5));
-          const uint32_t zw = __ldcg(WS(uint32_t, zbits) + (w0 >> 5));
+        for (int w = 0; w < warp; ++w) {
+          runk += ibuf[w];
+          runs += ibuf[8 + w];
+          runz += ibuf[16 + w];
+        }
+        __syncthreads();
+        const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
+        for (int w = wb; w < we; ++w) {
+          const int j = w * 32 + lane;
+          const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
+          const uint32_t zw = __ldcg(WS(uint32_t, zbits) + w);
           const bool keep = (word >> lane) & 1u;
           const bool nz = keep && nonzero2(ld_beta(cx, j));
           const unsigned lower = (1u << lane) - 1u;
           const int kpos = runk + __popc(word & lower);
           const unsigned smk = __ballot_sync(0xffffffffu, nz);
-          if (keep) WS(int, A)[kpos] = j;
+          if (keep) {
+            // certificate of a zero coefficient: slack / ||x_j|| with
+            // slack <= lambda - |x_j^T rho| (the check's c~ and its bound);
+            // nonzero coefficients are chain entries (never verified)
+            float sk = kSkChain;
+            if (!nz) {
+              const float nf = __ldcg(WS(float, nrmf) + j);
+              const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+              const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(__ldcg(WS(float, ctil) + j)), E));
+              sk = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
+            }
+            WS(float, sk)[kpos] = sk;
+            WS(float, mref)[kpos] = 0.f;
+            WS(int, A)[kpos] = j;
+          }
           if (nz) WS(int, sup0)[runs + __popc(smk & lower)] = kpos;
           if ((zw >> lane) & 1u) WS(int, zl_j)[runz + __popc(zw & lower)] = j;
           runk += __popc(word);
@@ -577,6 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
         ctl->q = totk;
         ctl->s = tots;
         ctl->nzl = totz;
+        ctl->mcur = 0.f;
       }
       scope_n = a.xtr_scope == 0 ? a.p : totk;
       GSYNC();
@@ -619,7 +678,16 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
             }
             store_rho_regs<NGC>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             __syncthreads();
-            if (tid == 0) ctl->nzl = 0;
+            if (tid == 0) {
+              float mv = ctl->mcur;
+              for (int i = 0; i < nz; ++i) {
+                const int jj = __ldcg(WS(int, zl_j) + i);
+                mv = __fadd_ru(mv, __fmul_ru(__double2float_ru(fabs(__ldcg(WS(double, zl_b) + jj))),
+                                             __ldcg(WS(float, nrmf) + jj)));
+              }
+              ctl->mcur = mv;
+              ctl->nzl = 0;
+            }
           }
         }
         for (int e = 0; e < a.f && epochs < a.max_epochs; ++e) {
@@ -651,6 +719,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
                 ctl->nc = nc;
                 ctl->round_end = rend;
                 ctl->fstar = kNoPos;
+                WS(float, msnap)[0] = ctl->mcur;
               }
               store_rho_regs<NGC>(cx, WS(float, snap), WS(float, snap) + a.ldw, rh, rl);  // snapshot 0
               __syncthreads();
@@ -669,43 +738,69 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
               const int chunk = (span + nwg - 1) / nwg;
               const int i0 = pos + gw * chunk, i1 = min(rend, i0 + chunk);
               if (span > 0 && i0 < i1) {
+                // a zero coefficient whose certificate survives the movement of
+                // the residual since it was issued stays zero without a read:
+                // |x_j^T rho| <= lambda - slack + ||x_j|| (M_now - M_ref) < lambda
+                const float mend = __ldcg(WS(float, msnap) + nc);
+                const float* skp = WS(float, sk);
+                float* mrp = WS(float, mref);
                 int seg = lower_bound_i(WS(int, chain), nc, i0);
-                int nextc = (seg < nc) ? __ldcg(WS(int, chain) + seg) : kNoPos;
                 float4 r4[NG];
                 int loaded = -1;
                 const float lamf = __double2float_rn(lam);
-                for (int i = i0; i < i1; ++i) {
-                  if (i == nextc) {
-                    ++seg;
-                    nextc = (seg < nc) ? __ldcg(WS(int, chain) + seg) : kNoPos;
-                    continue;
+                const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
+                bool stop_warp = false;
+                for (int base = i0; base < i1 && !stop_warp; base += 32) {
+                  const int il = base + lane;
+                  bool need = false;
+                  if (il < i1) {
+                    const float sk = __ldcg(skp + il);
+                    need = !(__fsub_ru(mend, __ldcg(mrp + il)) < sk);
                   }
-                  if (i > vload(ctl->fstar)) break;
-                  const float* sh = WS(float, snap) + (size_t)seg * 2 * a.ldw;
-                  if (loaded != seg) {
-#pragma unroll
-                    for (int k = 0; k < NG; ++k) {
-                      const int g = lane + 32 * k;
-                      r4[k] = (g < a.ld4) ? ldcg4(sh, g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                  unsigned needm = __ballot_sync(0xffffffffu, need);
+                  while (needm) {
+                    const int i = base + __ffs(needm) - 1;
+                    needm &= needm - 1;
+                    // fstar moves under other warps' atomicMin: one lane reads it
+                    // so that the whole warp takes the same branch before the
+                    // full-mask dot products below
+                    if (i > __shfl_sync(0xffffffffu, vload(ctl->fstar), 0)) {
+                      stop_warp = true;
+                      break;
                     }
-                    loaded = seg;
-                  }
-                  const int j = __ldcg(WS(int, A) + i);
-                  const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-                  const float nf = __ldcg(WS(float, nrmf) + j);
-                  const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
-                  bool enters;
-                  if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
-                  else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
-                  else {
-                    const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
-                    df2 nb, d;
-                    cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
-                    enters = !df_is_zero(d);
-                  }
-                  if (enters) {
-                    if (lane == 0) atomicMin(&ctl->fstar, i);
-                    break;
+                    while (seg < nc && __ldcg(WS(int, chain) + seg) < i) ++seg;
+                    const float* sh = WS(float, snap) + (size_t)seg * 2 * a.ldw;
+                    if (loaded != seg) {
+#pragma unroll
+                      for (int k = 0; k < NG; ++k) {
+                        const int g = lane + 32 * k;
+                        r4[k] = (g < a.ld4) ? ldcg4(sh, g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                      }
+                      loaded = seg;
+                    }
+                    const int j = __ldcg(WS(int, A) + i);
+                    const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
+                    const float nf = __ldcg(WS(float, nrmf) + j);
+                    const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
+                    bool enters;
+                    if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
+                    else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
+                    else {
+                      const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
+                      df2 nb, d;
+                      cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
+                      enters = !df_is_zero(d);
+                    }
+                    if (enters) {
+                      if (lane == 0) atomicMin(&ctl->fstar, i);
+                      stop_warp = true;
+                      break;
+                    }
+                    if (lane == 0) {
+                      const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
+                      WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
+                      mrp[i] = __ldcg(WS(float, msnap) + seg);
+                    }
                   }
                 }
               }
@@ -718,8 +813,11 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
               const int forced = vload(ctl->forced), si = vload(ctl->sup_idx);
               if (fst == kNoPos) {
                 if (tid == 0) {
-                  if (forced >= 0 && nonzero2(ld_beta(cx, __ldcg(WS(int, A) + forced))))
-                    WS(int, entered)[ctl->n_entered++] = forced;
+                  if (forced >= 0) {
+                    if (nonzero2(ld_beta(cx, __ldcg(WS(int, A) + forced)))) WS(int, entered)[ctl->n_entered++] = forced;
+                    else WS(float, sk)[forced] = kSkNone;  // stayed zero: verify it next pass
+                  }
+                  ctl->mcur = __ldcg(WS(float, msnap) + nc);
                   ctl->sup_idx = si + nc - (forced >= 0 ? 1 : 0);
                   ctl->pos = rend;
                   ctl->forced = -1;
@@ -734,8 +832,17 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
                 load_rho_regs<NGC>(cx, sh, sh + a.ldw, rh, rl);
                 __syncthreads();
                 if (tid == 0) {
-                  if (forced >= 0 && nonzero2(ld_beta(cx, __ldcg(WS(int, A) + forced))))
-                    WS(int, entered)[ctl->n_entered++] = forced;
+                  if (forced >= 0) {
+                    if (nonzero2(ld_beta(cx, __ldcg(WS(int, A) + forced)))) WS(int, entered)[ctl->n_entered++] = forced;
+                    else WS(float, sk)[forced] = kSkNone;
+                  }
+                  WS(float, sk)[fst] = kSkChain;  // the next round's forced chain entry
+                  // certificates issued on the undone branch stay valid if the
+                  // counter also pays for the way back: from any point e of
+                  // that branch, ||rho_t - rho_e|| <= (M_e - M_seg) + (new
+                  // movement) <= (2 M_end - M_seg - M_e) + (new movement)
+                  const float m_end = __ldcg(WS(float, msnap) + nc), m_seg = __ldcg(WS(float, msnap) + seg);
+                  ctl->mcur = __fsub_ru(__fmul_ru(2.0f, m_end), m_seg);
                   ctl->sup_idx = si + seg - (forced >= 0 ? 1 : 0);
                   ctl->forced = fst;
                   ctl->pos = fst;
@@ -763,6 +870,7 @@ __global__ void __launch_bounds__(kThreads, 1) path_kernel(Args a) {
               if (i < s) {
                 posv = __ldcg(sup + i);
                 keep = nonzero2(ld_beta(cx, __ldcg(WS(int, A) + posv)));
+                if (!keep) WS(float, sk)[posv] = kSkNone;  // left the support: a zero coefficient now
               }
               int tot;
               const int r = block_rank(keep, ibuf, &tot);
@@ -1008,7 +1116,8 @@ struct Layout {
 };
 enum {
   L_ctrl, L_cnt, L_part_l1, L_nrm, L_nrmf, L_ftab, L_bdf, L_b0df, L_rho_h, L_rho_l, L_rho0_h, L_rho0_l, L_ctil,
-  L_mask, L_A, L_sup0, L_sup1, L_chain, L_entered, L_oldb, L_recs, L_snap, L_zl_j, L_zl_b, L_zbits, L_yb, L_N
+  L_mask, L_A, L_sup0, L_sup1, L_chain, L_entered, L_oldb, L_recs, L_snap, L_zl_j, L_zl_b, L_zbits, L_yb, L_sk,
+  L_mref, L_msnap, L_N
 };
 
 Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
@@ -1047,6 +1156,9 @@ Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
   take(L_zl_b, sizeof(double) * p);
   take(L_zbits, sizeof(uint32_t) * words);
   take(L_yb, sizeof(double) * ldw);
+  take(L_sk, sizeof(float) * p);
+  take(L_mref, sizeof(float) * p);
+  take(L_msnap, sizeof(float) * (s_cap + 2));
   L.region = off;
   L.planes = planes ? 2 * align256(sizeof(float) * (size_t)ldw * (size_t)p) : 0;
   L.total = L.region + L.planes;
@@ -1085,6 +1197,9 @@ void set_offsets(Args& a, const Layout& L) {
   a.o_zl_b = L.o[L_zl_b];
   a.o_zbits = L.o[L_zbits];
   a.o_yb = L.o[L_yb];
+  a.o_sk = L.o[L_sk];
+  a.o_mref = L.o[L_mref];
+  a.o_msnap = L.o[L_msnap];
   a.ldw = L.ldw;
   a.s_cap = L.s_cap;
 }
