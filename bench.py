@@ -155,9 +155,15 @@ def _traffic_record():
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_1505_03410_gb300", "csrc", "path.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return rec if rec.get("source_sha256") == sha else None
+    return rec if rec.get("source_sha256") == path_kernel_sha() else None
+
+
+def path_kernel_sha():
+    """sha256 over the sources the path kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("path.cu", "cd_common.cuh", "dfloat.cuh", "device_util.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1505_03410_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def run_reference(args):
