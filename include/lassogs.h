@@ -151,7 +151,11 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
  *   beta_out_dev p x T x B FP64 (problem b's solution at lambda_t in
  *                column t + b*T), mask_out_dev words x T x B uint32 or NULL,
  *                stats_dev T x B records (index t + b*T).
- *   Other arguments as for lasso_path; beta0 is not taken (zero start).
+ *   beta0_dev    p x B FP64 starting points (column b = problem b's, leading
+ *                dimension ldb0 >= p) or NULL for the zero start; entries on
+ *                the problem's rows only enter through rho = y - X beta0.
+ *                With warm_start = 0 every lambda restarts from it.
+ *   Other arguments as for lasso_path.
  *
  * opts->gemm_dtype selects how the first check of every lambda gets X^T rho:
  *   LASSO_F32   one persistent launch; each resident CTA takes problems from
@@ -168,8 +172,23 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
  * lasso_path on the row-restricted problems, up to rounding. */
 lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* Y_dev, int64_t ldy,
                          const uint8_t* row_mask_dev, int64_t ldm, int64_t B, const double* lambda_ratios_dev,
-                         int32_t T, const lasso_opts* opts, double* beta_out_dev, uint32_t* mask_out_dev,
-                         lasso_path_stats* stats_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+                         int32_t T, const double* beta0_dev, int64_t ldb0, const lasso_opts* opts,
+                         double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
+                         void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* The correlation pass of one GAP SAFE check on its own: c = X^T r and
+ * m = ||c||_inf (Eq. (7) needs every |x_j^T rho|, the rescaling of Eq. (8)
+ * the maximum).  FP32 products accumulated in FP32, one HBM stream over X.
+ *
+ *   X     n x p FP32, column-major (column j at X + j*ldx), ldx >= n,
+ *         ldx % 4 == 0, 16-byte aligned; rows n..ldx-1 are ignored
+ *   r     n FP32 (16-byte aligned; entries past n are not read)
+ *   c     p FP32 out: c[j] = x_j^T r, each within
+ *         (4 ceil(n/128) + 6) 2^-24 sum_i |x_ij r_i| of the exact value
+ *   cmax  1 FP32 out (may be NULL): max_j |c[j]|
+ * 1 <= n <= 2048.  Asynchronous on `stream`; errors as for lasso_path. */
+lasso_status lasso_correlations_f32(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const float* r_dev,
+                                    float* c_dev, float* cmax_dev, void* stream);
 
 /* Batched correlations C = X^T R for B residuals at once -- the first GAP
  * SAFE check of every problem of a batch is this product (Eq. (8) needs

@@ -88,7 +88,7 @@ def _bind(path):
     lib.orc_cd_pass.restype = None
     lib.orc_lasso_path.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, P, P]
     lib.orc_lasso_path.restype = ctypes.c_int
-    lib.orc_lasso_batch.argtypes = [P, I64, I64, I64, P, P, I64, P, I32, P, P, P, P]
+    lib.orc_lasso_batch.argtypes = [P, I64, I64, I64, P, P, I64, P, I32, P, P, P, P, P]
     lib.orc_lasso_batch.restype = ctypes.c_int
     return lib
 
@@ -224,9 +224,10 @@ def lasso_path(X, y, ratios, beta0=None, n=None, log_checks=0, **opt):
     return out
 
 
-def lasso_batch(X, Y, ratios, row_mask=None, n=None, **opt):
+def lasso_batch(X, Y, ratios, row_mask=None, n=None, beta0=None, **opt):
     """Independent paths over one design: problem b uses rows with
-    row_mask[b, i] != 0 and response Y[b] (shape (B, n)).  Returns
+    row_mask[b, i] != 0, response Y[b] (shape (B, n)) and starting point
+    beta0[b] (shape (B, p), zeros when None).  Returns
     beta (B, T, p), mask (B, T, words), stats dict of (B, T) arrays."""
     lib = _load()
     Xc, n, p, ldx = _colmajor64(X, n)
@@ -241,7 +242,8 @@ def lasso_batch(X, Y, ratios, row_mask=None, n=None, **opt):
     mask_out = np.empty((B, T, W), dtype=np.uint32)
     stats = np.empty((B, T, NF))
     o = _opts(**opt)
-    rc = lib.orc_lasso_batch(_ptr(Xc), n, p, ldx, _ptr(Y), _ptr(rm), B, _ptr(ratios), T,
+    b0 = None if beta0 is None else np.ascontiguousarray(beta0, dtype=np.float64).reshape(B, p)
+    rc = lib.orc_lasso_batch(_ptr(Xc), n, p, ldx, _ptr(Y), _ptr(rm), B, _ptr(ratios), T, _ptr(b0),
                              ctypes.byref(o), _ptr(beta_out), _ptr(mask_out), _ptr(stats))
     return dict(beta=beta_out, mask=mask_out,
                 stats={f: stats[:, :, i] for i, f in enumerate(STAT_FIELDS)}, status=int(rc))

@@ -325,12 +325,14 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
 /* Many independent paths over one design X (the batched workload): problem b
  * uses the rows i with row_mask[i + b*n] != 0 (all rows when row_mask is
  * NULL) and the response Y[:, b] (n x B, column-major, ld n; entries outside
- * the row subset are ignored).  Each problem is the plain path above on its
- * own row subset, with its own lambda_max; outputs are stacked by problem:
+ * the row subset are ignored) and starts from beta0[b*p .. b*p + p) (zeros
+ * when beta0 is NULL).  Each problem is the plain path above on its own row
+ * subset, with its own lambda_max; outputs are stacked by problem:
  * beta_out p*T*B, mask_out words*T*B, stats ST_NFIELDS*T*B. */
 int orc_lasso_batch(const double* X, int64_t n, int64_t p, int64_t ldx, const double* Y,
                     const uint8_t* row_mask, int64_t B, const double* ratios, int32_t T,
-                    const orc_opts* o, double* beta_out, uint32_t* mask_out, double* stats) {
+                    const double* beta0, const orc_opts* o, double* beta_out, uint32_t* mask_out,
+                    double* stats) {
   int64_t words = (p + 31) / 32;
   int status = ORC_OK;
   double* Xs = (double*)malloc(sizeof(double) * (size_t)(n * p));
@@ -351,7 +353,7 @@ int orc_lasso_batch(const double* X, int64_t n, int64_t p, int64_t ldx, const do
         ++r;
       }
     }
-    int rc = orc_lasso_path(Xs, m, p, m, ys, ratios, T, NULL, o, beta_out + b * p * T,
+    int rc = orc_lasso_path(Xs, m, p, m, ys, ratios, T, beta0 ? beta0 + b * p : NULL, o, beta_out + b * p * T,
                             mask_out ? mask_out + b * words * T : NULL,
                             stats + b * ST_NFIELDS * T, NULL);
     if (rc != ORC_OK && status == ORC_OK) status = rc;

@@ -127,8 +127,8 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
 
 lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
                          const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
-                         const lasso_opts* opts, double* beta_out, uint32_t* mask_out, lasso_path_stats* stats,
-                         void* ws, size_t ws_bytes, void* stream) {
+                         const double* beta0, int64_t ldb0, const lasso_opts* opts, double* beta_out,
+                         uint32_t* mask_out, lasso_path_stats* stats, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
   lasso_opts o;
   if (opts) o = *opts;
@@ -145,11 +145,12 @@ lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, cons
     return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: X needs ldx >= n, ldx %% 4 == 0 and a 16-byte aligned base");
   if (ldy < n) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: ldy < n");
   if (row_mask && ldm < n) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: ldm < n");
+  if (beta0 && ldb0 < p) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: ldb0 < p");
   if (!aligned(Y, 8) || !aligned(ratios, 8) || !aligned(beta_out, 8) || !aligned(stats, 8) ||
-      (mask_out && !aligned(mask_out, 4)))
+      (mask_out && !aligned(mask_out, 4)) || (beta0 && !aligned(beta0, 8)))
     return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: misaligned vector argument");
   if (!ws || !aligned(ws, 256)) return set_error(LASSO_ERR_WORKSPACE, "lasso_batch: workspace must be non-NULL and 256-byte aligned");
-  return batch_launch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, ratios, T, o, beta_out, mask_out, stats, ws, ws_bytes,
+  return batch_launch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, ratios, T, beta0, ldb0, o, beta_out, mask_out, stats, ws, ws_bytes,
                       static_cast<cudaStream_t>(stream));
 }
 

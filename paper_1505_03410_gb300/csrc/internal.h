@@ -25,7 +25,8 @@ lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, 
                              int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream);
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
                           const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
-                          const lasso_opts& o, double* beta_out, uint32_t* mask_out, lasso_path_stats* stats,
+                          const double* beta0, int64_t ldb0, const lasso_opts& o, double* beta_out,
+                          uint32_t* mask_out, lasso_path_stats* stats,
                           void* ws, size_t ws_bytes, cudaStream_t stream);
 
 }  // namespace lassogs

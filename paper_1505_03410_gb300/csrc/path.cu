@@ -88,6 +88,8 @@ struct Args {
   int B;
   long long ldy, ldm;
   const uint8_t* rmask;
+  const double* beta0;  // starting points beta0[j + b * ldb0], or null
+  long long ldb0;
   int* queue;       // next problem to take
   double tol;       // gap_tol_rel
   // lockstep batches: one launch per lambda range [t0, t1), workspace region
@@ -139,8 +141,13 @@ __device__ __forceinline__ uint32_t chain_row_bits(const Args& a, int b) {
   return bits;
 }
 
+// rows of a batched problem's residual held by one thread while beta0 is applied
+constexpr int kBatchRowsPerThread = 8;
+static_assert(kBatchRowsPerThread * kThreads >= kMaxRows, "a thread's rows must cover n <= kMaxRows");
+
 // Per-problem set-up of a batched CTA (the single path does this with the
-// precompute kernels): y restricted to the problem's rows, rho = y, ||y||^2,
+// precompute kernels): y restricted to the problem's rows, rho = y - X beta0,
+// ||y||^2,
 // and for every column the norm over those rows and x_j^T y, whose largest
 // magnitude is lambda_max (Sec. 1.2).  FP64 accumulation.
 template <bool XLO>
@@ -203,8 +210,64 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
       const df2 iv = df_from_double(s2 > 0.0 ? __drcp_rn(s2) : 0.0);
       ftab[j] = make_float4(iv.h, iv.l, 0.f, 0.f);
       if (isfinite(sy)) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(fabs(sy)));
-      bdf[j] = make_float2(0.f, 0.f);
-      b0df[j] = make_float2(0.f, 0.f);
+      const df2 bd = df_from_double(a.beta0 ? a.beta0[j + (size_t)b * a.ldb0] : 0.0);
+      bdf[j] = make_float2(bd.h, bd.l);
+      b0df[j] = make_float2(bd.h, bd.l);
+    }
+  }
+  if (a.beta0 != nullptr) {
+    // rho = y - X beta0 on the problem's rows: the nonzero terms are
+    // subtracted in ascending j, each product and difference rounded once
+    __shared__ int s_j[kThreads];
+    __shared__ double s_b[kThreads];
+    __shared__ int s_cnt[kThreads / 32];
+    double racc[kBatchRowsPerThread];
+    unsigned inrow = 0;
+#pragma unroll
+    for (int k = 0; k < kBatchRowsPerThread; ++k) {
+      const int i = tid + k * kThreads;
+      const bool in = i < a.n && (a.rmask == nullptr || a.rmask[i + (size_t)b * a.ldm] != 0);
+      inrow |= (in ? 1u : 0u) << k;
+      racc[k] = in ? yb[i] : 0.0;
+    }
+    const double* b0 = a.beta0 + (size_t)b * a.ldb0;
+    for (int base = 0; base < a.p; base += kThreads) {
+      const int j = base + tid;
+      const double v = j < a.p ? b0[j] : 0.0;
+      finite = finite && isfinite(v);
+      int tot;
+      const int r = block_rank(v != 0.0, s_cnt, &tot);
+      if (v != 0.0) {
+        s_j[r] = j;
+        s_b[r] = v;
+      }
+      __syncthreads();
+      for (int c = 0; c < tot; ++c) {
+        const long long off = (long long)s_j[c] * a.ldx;
+        const double bv = s_b[c];
+#pragma unroll
+        for (int k = 0; k < kBatchRowsPerThread; ++k) {
+          if ((inrow >> k) & 1u) {
+            const int i = tid + k * kThreads;
+            double x = (double)a.Xh[off + i];
+            if (XLO) x = __dadd_rn(x, (double)a.Xl[off + i]);
+            racc[k] = __dsub_rn(racc[k], __dmul_rn(bv, x));
+          }
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < kBatchRowsPerThread; ++k) {
+      const int i = tid + k * kThreads;
+      if ((inrow >> k) & 1u) {
+        finite = finite && isfinite(racc[k]);
+        const df2 d = df_from_double(racc[k]);
+        rh[i] = d.h;
+        rl[i] = d.l;
+        r0h[i] = d.h;
+        r0l[i] = d.l;
+      }
     }
   }
   if (!finite) atomicExch(&ctl->nonfinite, 1);
@@ -1074,7 +1137,7 @@ __global__ void pack_x_kernel(const float* __restrict__ X, long long ldx, int n,
 // residuals of the B problems: from the masked responses (first lambda) or
 // from the FP32 high planes of the residuals kept in each problem's region
 __global__ void pack_r_kernel(const double* Y, long long ldy, const uint8_t* rmask, long long ldm, const char* ws,
-                              size_t region, size_t o_rho_h, int n, int B, int L, int from_y,
+                              size_t region, size_t o_rho, int n, int B, int L, int from_y,
                               __nv_bfloat16* __restrict__ R3) {
   const long long total = (long long)B * L;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
@@ -1085,7 +1148,7 @@ __global__ void pack_r_kernel(const double* Y, long long ldy, const uint8_t* rma
         const bool in = rmask == nullptr || rmask[i + (size_t)b * ldm] != 0;
         v = in ? (float)Y[i + (size_t)b * ldy] : 0.f;
       } else {
-        v = reinterpret_cast<const float*>(ws + (size_t)b * region + o_rho_h)[i];
+        v = reinterpret_cast<const float*>(ws + (size_t)b * region + o_rho)[i];
       }
     }
     __nv_bfloat16 h, l;
@@ -1408,7 +1471,8 @@ size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep) {
 
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
                           const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
-                          const lasso_opts& o, double* beta_out, uint32_t* mask_out, lasso_path_stats* stats,
+                          const double* beta0, int64_t ldb0, const lasso_opts& o, double* beta_out,
+                          uint32_t* mask_out, lasso_path_stats* stats,
                           void* ws, size_t ws_bytes, cudaStream_t stream) {
   DevInfo d{};
   lasso_status st = dev_info(d);
@@ -1429,6 +1493,8 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   a.ldy = ldy;
   a.rmask = row_mask;
   a.ldm = ldm;
+  a.beta0 = beta0;
+  a.ldb0 = ldb0;
   a.queue = reinterpret_cast<int*>(base);
   a.ratios = ratios;
   a.beta_out = beta_out;
@@ -1467,11 +1533,20 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   pack_x_kernel<<<d.sms * 8, 256, 0, stream>>>(X, ldx, (int)n, (int)p, (int)Lk, X3);
   CUDA_TRY(cudaGetLastError());
   for (int t = 0; t < T; ++t) {
-    pack_r_kernel<<<d.sms * 4, 256, 0, stream>>>(Y, ldy, row_mask, ldm, a.ws, a.cta_bytes, a.o_rho_h, (int)n, (int)B,
-                                                 (int)Lk, t == 0 ? 1 : 0, R3);
-    CUDA_TRY(cudaGetLastError());
-    st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream);
-    if (st != LASSO_OK) return st;
+    // the product must be taken on the residual the lambda starts from: y at
+    // t = 0 (zero start), rho0 = y - X beta0 when every lambda restarts, else
+    // the previous lambda's final residual.  At t = 0 with beta0 the residual
+    // is formed inside the launch, so that first check runs the FP32 pass.
+    const bool use_gemm = !(t == 0 && beta0 != nullptr);
+    if (use_gemm) {
+      pack_r_kernel<<<d.sms * 4, 256, 0, stream>>>(Y, ldy, row_mask, ldm, a.ws, a.cta_bytes,
+                                                   o.warm_start ? a.o_rho_h : a.o_rho0_h, (int)n, (int)B, (int)Lk,
+                                                   t == 0 ? 1 : 0, R3);
+      CUDA_TRY(cudaGetLastError());
+      st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream);
+      if (st != LASSO_OK) return st;
+    }
+    a.cfirst = use_gemm ? C : nullptr;
     CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
     a.t0 = t;
     a.t1 = t + 1;

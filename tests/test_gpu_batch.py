@@ -25,13 +25,14 @@ def pkg():
     return p
 
 
-def run_gpu_batch(pkg, XT, n, Y, rmask, ratios, **opt):
+def run_gpu_batch(pkg, XT, n, Y, rmask, ratios, beta0=None, **opt):
     dev = torch.device("cuda:0")
     Xd = torch.from_numpy(np.ascontiguousarray(XT, dtype=np.float32)).to(dev)
     Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float64)).to(dev)
     Md = None if rmask is None else torch.from_numpy(np.ascontiguousarray(rmask, dtype=np.uint8)).to(dev)
     r = torch.from_numpy(np.ascontiguousarray(ratios, dtype=np.float64)).to(dev)
-    out = pkg.solve_batch(Xd, Yd, r, n=n, row_mask=Md, opts=pkg.lasso_default_opts(**opt))
+    b0 = None if beta0 is None else torch.from_numpy(np.ascontiguousarray(beta0, dtype=np.float64)).to(dev)
+    out = pkg.solve_batch(Xd, Yd, r, n=n, row_mask=Md, beta0=b0, opts=pkg.lasso_default_opts(**opt))
     torch.cuda.synchronize()
     B, T = Y.shape[0], len(ratios)
     st = pkg.stats_to_numpy(out["stats"]).reshape(B, T)
@@ -124,4 +125,27 @@ def test_batch_workload3_full_size_prefix(pkg, gemm):
     opt = dict(gap_tol_rel=w["tol"], xtr_scope=1, screen_period=w["f"])
     g = run_gpu_batch(pkg, w["XT"], w["n"], w["Y"], w["row_mask"], ratios, gemm_dtype=gemm, **opt)
     o = oracle.lasso_batch(w["XT"], w["Y"], ratios, row_mask=w["row_mask"], n=w["n"], **opt)
+    check_batch(g, o)
+
+
+@pytest.mark.parametrize("gemm", GEMM)
+@pytest.mark.parametrize("warm", [1, 0])
+def test_batch_beta0(pkg, gemm, warm):
+    """Per-problem starting points (Sec. 3.3 warm start taken from outside,
+    e.g. a learned initialiser): rho = y - X beta0 on the problem's rows;
+    with warm_start = 0 every lambda restarts from beta0.  The grid starts
+    below lambda_max: there, from a nonzero start, the update of the feature
+    attaining lambda_max lands exactly on the soft-threshold boundary and its
+    sign of rounding (+-1e-16 or 0) is not a property of the method."""
+    prob, Y, rmask = _subsample_problem(207, 150, 1200, 6, correlated=True)
+    rng = np.random.default_rng(207)
+    beta0 = np.zeros((6, 1200))
+    for b in range(6):
+        idx = rng.choice(1200, size=int(rng.integers(0, 40)), replace=False)
+        beta0[b, idx] = rng.standard_normal(idx.size) * 0.3
+    beta0[3] = 0.0  # one problem from zero
+    ratios = oracle.lambda_ratios(9, 1.5)[1:]
+    opt = dict(gap_tol_rel=1e-9, warm_start=warm)
+    g = run_gpu_batch(pkg, prob["XT"], 150, Y, rmask, ratios, beta0=beta0, gemm_dtype=gemm, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=150, beta0=beta0, **opt)
     check_batch(g, o)
