@@ -136,7 +136,7 @@ def workload3(seed=1003, n=1000, p=20000, B=256, k=30):
                 row_mask=row_mask, beta_star=bstar, T=50, delta=2.0, f=10, tol=1e-6)
 
 
-def workload4(seed=1004, n=300, p=10000, n_train=200000, n_eval=4096):
+def workload4(seed=1004, n=300, p=10000, n_train=200000, n_eval=4096, k_range=(5, 50)):
     """Learned warm start on a fixed design: Gaussian 300 x 10000 FP32
     unit-norm; each y from its own beta* with k ~ U{5..50} N(0,1) entries and
     SNR ~ U[2,10].  Returns the design and a response sampler."""
@@ -147,7 +147,7 @@ def workload4(seed=1004, n=300, p=10000, n_train=200000, n_eval=4096):
         r = np.random.default_rng(seed * 1000 + seed_offset)
         Y = np.empty((count, n))
         for i in range(count):
-            k = int(r.integers(5, 51))
+            k = int(r.integers(k_range[0], k_range[1] + 1))
             bstar = sparse_truth(r, p, k)
             signal = _matvec(XT, n, bstar)
             snr = r.uniform(2.0, 10.0)

@@ -81,10 +81,14 @@ def loss(betaL, Tgt):
     return 0.5 * float(np.sum((betaL - Tgt) ** 2)) / B
 
 
-def backward(X, W, D, tau, Ytil, Tgt):
+def backward(X, W, D, tau, Ytil, Tgt, masks=None):
     """Loss and its gradients (dW, dD, dtau) by the chain rule through the L
-    layers, taken from the last layer to the first.  The derivative of ST at
-    the kink |z| = tau is taken as 0 (a set of measure zero)."""
+    layers, taken from the last layer to the first.  The derivative of ST in
+    z is the indicator [|z_l| > tau_l] (0 at the kink, a set of measure zero).
+    masks, when given, is the list of per-layer indicators to use instead:
+    a decision that floating point takes is then taken in the precision of
+    the implementation under test (its own indicators), while every
+    arithmetic step stays FP64."""
     betaL, cache = forward(X, W, D, tau, Ytil)
     B = Ytil.shape[0]
     g = (betaL - Tgt) / B                # d loss / d beta^L
@@ -93,7 +97,8 @@ def backward(X, W, D, tau, Ytil, Tgt):
     dtau = np.zeros_like(tau)
     for l in range(len(tau) - 1, -1, -1):
         u, v, z = cache[l]
-        gz = g * (np.abs(z) > tau[l])    # through ST in z
+        ind = (np.abs(z) > tau[l]) if masks is None else masks[l]
+        gz = g * ind                     # through ST in z
         dtau[l] = -np.sum(np.sign(z) * gz)
         dD[l] = np.sum(gz * v, axis=0)
         gv = D[l] * gz

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblassogs.so")
-SOURCES = ["api.cu", "path.cu", "static_scratch.cu", "gemm_tc.cu"]
+SOURCES = ["api.cu", "path.cu", "static_scratch.cu", "gemm_tc.cu", "lista.cu", "xtr.cu"]
 HEADERS = ["dfloat.cuh", "device_util.cuh", "cd_common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -49,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of liblassogs.so."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "lassogs.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", h)
+                                                        for h in ("lassogs.h", "lista.h")]
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

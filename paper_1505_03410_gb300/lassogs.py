@@ -31,7 +31,7 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 # every symbol include/lassogs.h declares
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
             "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch",
-            "lasso_correlations_bf16")
+            "lasso_correlations_bf16", "lasso_correlations_f32")
 
 
 class LassoError(RuntimeError):
@@ -89,11 +89,13 @@ def load(path: str | None = None):
             lib.lasso_path_static.restype = ctypes.c_int
             lib.lasso_batch_workspace_size.argtypes = [I64, I64, I64, ctypes.POINTER(LassoOpts)]
             lib.lasso_batch_workspace_size.restype = SZ
-            lib.lasso_batch.argtypes = [V, I64, I64, I64, V, I64, V, I64, I64, V, I32, ctypes.POINTER(LassoOpts),
-                                        V, V, V, V, SZ, V]
+            lib.lasso_batch.argtypes = [V, I64, I64, I64, V, I64, V, I64, I64, V, I32, V, I64,
+                                        ctypes.POINTER(LassoOpts), V, V, V, V, SZ, V]
             lib.lasso_batch.restype = ctypes.c_int
             lib.lasso_correlations_bf16.argtypes = [V, I64, I64, I64, V, I64, I64, V, I64, V, SZ, V]
             lib.lasso_correlations_bf16.restype = ctypes.c_int
+            lib.lasso_correlations_f32.argtypes = [V, I64, I64, I64, V, V, V, V]
+            lib.lasso_correlations_f32.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
             lib.lasso_last_error.restype = ctypes.c_char_p
             _lib = lib
@@ -159,24 +161,26 @@ def lasso_batch_workspace_size(n: int, p: int, B: int, opts: LassoOpts | None = 
                                                  ctypes.byref(opts) if opts is not None else None))
 
 
-def lasso_batch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, lambda_ratios, T, opts, beta_out, mask_out, stats,
-                workspace, workspace_bytes, stream) -> int:
+def lasso_batch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, lambda_ratios, T, beta0, ldb0, opts, beta_out, mask_out,
+                stats, workspace, workspace_bytes, stream) -> int:
     """Direct call of the batched C entry point (pointers as integers)."""
     def vp(x):
         return None if x is None or x == 0 else ctypes.c_void_p(int(x))
     return _check(load().lasso_batch(vp(X), int(n), int(p), int(ldx), vp(Y), int(ldy), vp(row_mask), int(ldm),
-                                     int(B), vp(lambda_ratios), int(T),
+                                     int(B), vp(lambda_ratios), int(T), vp(beta0), int(ldb0),
                                      ctypes.byref(opts) if opts is not None else None, vp(beta_out),
                                      vp(mask_out), vp(stats), vp(workspace), int(workspace_bytes), vp(stream)))
 
 
-def solve_batch(XT, Y, ratios, n=None, row_mask=None, opts=None, workspace=None, stream=None, want_mask=True):
+def solve_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, workspace=None, stream=None,
+                want_mask=True):
     """Allocate outputs as torch CUDA tensors and run lasso_batch.
 
     XT: (p, ldx) float32 CUDA tensor (column-major design); Y: (B, ldy) float64
     CUDA tensor (row b = problem b's responses); row_mask: (B, ldm) uint8 or
-    None; ratios: (T,) float64.  Returns beta (B, T, p), mask (B, T, words),
-    stats (uint8 bytes of B*T records)."""
+    None; beta0: (B, ldb0) float64 starting points or None; ratios: (T,)
+    float64.  Returns beta (B, T, p), mask (B, T, words), stats (uint8 bytes
+    of B*T records)."""
     import torch
     assert XT.is_cuda and XT.is_contiguous() and XT.dtype == torch.float32
     p, ldx = XT.shape
@@ -193,8 +197,12 @@ def solve_batch(XT, Y, ratios, n=None, row_mask=None, opts=None, workspace=None,
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     s = stream if stream is not None else torch.cuda.current_stream(dev)
+    if beta0 is not None:
+        assert beta0.is_cuda and beta0.is_contiguous() and beta0.dtype == torch.float64 and beta0.shape[0] == B
     lasso_batch(XT.data_ptr(), n, p, ldx, Y.data_ptr(), ldy, row_mask.data_ptr() if row_mask is not None else None,
-                row_mask.shape[1] if row_mask is not None else 0, B, ratios.data_ptr(), T, opts, beta_out.data_ptr(),
+                row_mask.shape[1] if row_mask is not None else 0, B, ratios.data_ptr(), T,
+                beta0.data_ptr() if beta0 is not None else None, beta0.shape[1] if beta0 is not None else 0,
+                opts, beta_out.data_ptr(),
                 mask_out.data_ptr() if mask_out is not None else None, stats.data_ptr(), workspace.data_ptr(),
                 workspace.numel(), s.cuda_stream)
     return dict(beta=beta_out, mask=mask_out, stats=stats, workspace=workspace)
@@ -206,6 +214,14 @@ def lasso_correlations_bf16(X_bf16, n, p, ldx, R_bf16, ldr, B, C, ldc, workspace
         return None if x is None or x == 0 else ctypes.c_void_p(int(x))
     return _check(load().lasso_correlations_bf16(vp(X_bf16), int(n), int(p), int(ldx), vp(R_bf16), int(ldr), int(B),
                                                  vp(C), int(ldc), vp(workspace), int(workspace_bytes), vp(stream)))
+
+
+def lasso_correlations_f32(X, n, p, ldx, r, c, cmax, stream) -> int:
+    """c = X^T r and cmax = ||c||_inf (pointers as integers)."""
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    return _check(load().lasso_correlations_f32(vp(X), int(n), int(p), int(ldx), vp(r), vp(c), vp(cmax),
+                                                vp(stream)))
 
 
 def stats_to_numpy(stats_tensor) -> np.ndarray:

@@ -1,5 +1,6 @@
 """The C-ABI boundary without a GPU: the library loads, exports every symbol
-include/lassogs.h declares, and its host-only logic behaves as documented."""
+include/lassogs.h and include/lista.h declare, and its host-only logic behaves
+as documented."""
 import ctypes
 import os
 import re
@@ -27,14 +28,15 @@ def _declared_functions():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(lasso_\w+)\s*\(", src, flags=re.M)
+            names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b((?:lasso|lista)_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
 def test_every_declared_symbol_is_exported(pkg):
     lib = ctypes.CDLL(pkg.lassogs.LIB_PATH)
     declared = _declared_functions()
-    assert set(declared) >= set(pkg.EXPORTED)
+    assert set(declared) >= set(pkg.EXPORTED) | set(pkg.lista.EXPORTED)
+    assert {n for n in declared if n.startswith("lista_")} == set(pkg.lista.EXPORTED)
     for name in declared:
         assert hasattr(lib, name), f"{name} declared in include/ but not exported"
 
@@ -112,3 +114,26 @@ def test_product_has_no_cpu_fallback(pkg, tmp_path):
             mod.load(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_lista_host_checks(pkg):
+    """Sizes and NULL arguments of the learned-warm-start entry points are
+    rejected on the host, before any CUDA call."""
+    L = pkg.lista
+    assert L.lista_workspace_size(0, 10, 8, 4) == 0
+    assert L.lista_workspace_size(10, 10, 0, 4) == 0
+    assert L.lista_workspace_size(10, 10, 65, 4) == 0
+    # the cache of a training batch: L x B x (n + 2p) floats at least
+    assert L.lista_workspace_size(300, 10000, 8, 256) >= 8 * 256 * (300 + 2 * 10000) * 4
+    with pytest.raises(pkg.LassoError) as e:
+        L.lista_forward(None, 10, 20, 10, None, None, None, 8, None, 10, 4, None, 0, None, 0, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError) as e:
+        L.lista_backward(None, 10, 20, 10, None, None, None, 0, 4, None, None, None, None, None, None, None, 0, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError) as e:
+        L.lista_adam(None, None, None, None, 10, 1, 1e-3, 0.9, 0.999, 1e-8, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError) as e:
+        L.lista_adam(1, 1, 1, 1, 10, 0, 1e-3, 0.9, 0.999, 1e-8, None)  # t must be >= 1
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
