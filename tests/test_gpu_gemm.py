@@ -49,3 +49,29 @@ def test_correlations_bf16(pkg, n, p, B):
     got = C.double().cpu().numpy()
     assert np.all(np.isfinite(got))
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+@pytest.mark.parametrize("n,p,ldx", [(500, 50000, 500), (37, 1001, 40), (130, 3000, 132), (1000, 20000, 1000),
+                                     (2048, 777, 2048), (1, 5, 4), (129, 64, 132)])
+def test_correlations_f32(pkg, n, p, ldx):
+    """c = X^T r for an FP32 design: each c_j within (4 ceil(n/128) + 6) 2^-24
+    sum_i |x_ij r_i| of the FP64 product of the same FP32 values, the maximum
+    equal to max_j |c_j|, and padding rows of X ignored."""
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(n * 7 + p)
+    X = rng.standard_normal((p, ldx)).astype(np.float32)
+    X[:, n:] = np.nan  # padding rows must not be read into the sums
+    r = rng.standard_normal(n).astype(np.float32)
+    Xd = torch.from_numpy(X).to(dev)
+    rd = torch.from_numpy(r).to(dev)
+    c = torch.full((p,), float("nan"), dtype=torch.float32, device=dev)
+    m = torch.zeros((1,), dtype=torch.float32, device=dev)
+    pkg.lasso_correlations_f32(Xd.data_ptr(), n, p, ldx, rd.data_ptr(), c.data_ptr(), m.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    cg = c.cpu().numpy().astype(np.float64)
+    X64 = X[:, :n].astype(np.float64)
+    exact = X64 @ r.astype(np.float64)
+    bound = (4 * ((n + 127) // 128) + 6) * 2.0 ** -24 * (np.abs(X64) @ np.abs(r.astype(np.float64)))
+    assert np.all(np.abs(cg - exact) <= bound), float(np.max(np.abs(cg - exact) / bound))
+    assert float(m.item()) == float(np.max(np.abs(cg)))
