@@ -15,6 +15,10 @@ Keys beyond the base contract:
                 duration, against the measured HBM copy peak
   cpu_baseline  the FP64 oracle on the host cores, a bounded sample of the
                 same path (its first 50 lambdas)
+  xtr_pass      the standalone correlation pass c = X^T r (the check's HBM
+                stream) timed per launch, L2 flushed, against the HBM peak
+  tuned_vs_plain  the batched solver (256 stability-selection problems x 50
+                lambdas) against the plain single-problem path on a sample
   e2e           the same metric through the C-ABI with the inputs copied from
                 pinned host memory and beta/stats copied back inside the step
   clocks        nvidia-smi SM clocks and throttle reasons sampled during the
@@ -49,6 +53,14 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lambdas", type=int, default=0,
                     help="solve only the first K lambdas of the grid (a smaller case for profiling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the correlation-pass roofline and the tuned-vs-plain comparison")
+    ap.add_argument("--no-tuned", action="store_true", help="skip the tuned-vs-plain comparison")
+    ap.add_argument("--learned", type=int, default=0, metavar="N_TRAIN",
+                    help="also measure the learned warm start on the 300 x 10000 design: train on N_TRAIN "
+                         "solver solutions, then solve 1024 held-out responses from zero and from the net")
+    ap.add_argument("--plain-sample", type=int, default=8,
+                    help="problems of the batched workload timed one at a time on the plain path")
     return ap.parse_args()
 
 
@@ -342,11 +354,168 @@ def run_ours(args):
             "gpu_launches": 5 * args.steps, "clocks": clk,
             "solves_per_step": solves_per_step, "epochs_per_step": int(st["epochs"].sum()),
             "checks_per_step": int(st["checks"].sum())}
+    if ws == 1 and not args.no_extras:
+        line["xtr_pass"] = [
+            _xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, XT, n, p, w["ldx"],
+                      "toeplitz-500x50000-f32 (100 MB, the bench design)")]
+        g = torch.Generator(device=dev)
+        g.manual_seed(1005)
+        Xbig = torch.randn((100000, 2000), generator=g, device=dev, dtype=torch.float32)
+        line["xtr_pass"].append(_xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, Xbig, 2000, 100000, 2000,
+                                          "gaussian-2000x100000-f32 (800 MB, the large multi-RHS design)"))
+        del Xbig
+        if not args.no_tuned:
+            line["tuned_vs_plain"] = _tuned_vs_plain(pkg, torch, dev, stream, flush, args.plain_sample)
+    if ws == 1 and args.learned > 0:
+        line["learned_warm_start"] = _learned(pkg, torch, dev, stream, args.learned)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, XT, n, p, ldx, label, reps=10):
+    """Event-timed launches of the standalone correlation pass (c = X^T r,
+    ||c||_inf), L2 flushed before each; algorithmic bytes = X + r + c.
+    The flush writes 512 MiB and then reads 256 MB, so L2 holds clean lines
+    when the timed launch starts and none of its DRAM time goes to writing
+    back the flush's dirty lines."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    r = torch.randn((n,), generator=g, device=dev, dtype=torch.float32)
+    c = torch.empty((p,), dtype=torch.float32, device=dev)
+    m = torch.empty((1,), dtype=torch.float32, device=dev)
+    clean = torch.ones((64 << 20,), dtype=torch.float32, device=dev)
+    times = []
+    for k in range(3 + reps):
+        flush.fill_(k & 0xff)
+        clean.sum()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.lasso_correlations_f32(XT.data_ptr(), n, p, ldx, r.data_ptr(), c.data_ptr(), m.data_ptr(),
+                                   stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 3:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    nbytes = 4.0 * n * p + 4.0 * n + 4.0 * p
+    ach = nbytes / (ms / 1e3) / 1e9
+    return {"workload": label, "n": n, "p": p, "bytes_per_launch": nbytes, "ms_per_launch": ms,
+            "launches": reps, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "l2": "flushed before each launch (512 MiB write, then a 256 MB read)"}
+
+
+def _tuned_vs_plain(pkg, torch, dev, stream, flush, sample):
+    """Stability-selection workload (256 row-subset problems, 50 lambdas):
+    the batched solver in both modes against the plain single-problem path run
+    one problem at a time on a bounded sample."""
+    import numpy as np
+    import gen
+    w = gen.workload3()
+    n, p, B, T = w["n"], w["p"], w["Y"].shape[0], w["T"]
+    XT = torch.from_numpy(w["XT"]).to(dev)
+    Y = torch.from_numpy(w["Y"]).to(dev)
+    M = torch.from_numpy(w["row_mask"]).to(dev)
+    ratios = torch.from_numpy(pkg.lasso_lambda_grid(T, w["delta"])).to(dev)
+    out = {"workload": w["name"] + ": Gaussian 1000x20000 FP32, 256 row subsets of U{400..1000}, beta* 30-sparse, "
+           "SNR 5, T=50 to lambda_max/100, check every 10 passes, gap<=1e-6*||y||^2", "problems": B, "T": T}
+    launches = 0
+    for name, gd in (("batched_fp32", pkg.LASSO_F32), ("batched_split_bf16_tc", pkg.LASSO_BF16)):
+        opts = pkg.lasso_default_opts(xtr_scope=1, gemm_dtype=gd, screen_period=w["f"], gap_tol_rel=w["tol"])
+        pkg.solve_batch(XT, Y[:8].contiguous(), ratios, n=n, row_mask=M[:8].contiguous(), opts=opts)
+        torch.cuda.synchronize()
+        flush.fill_(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = pkg.solve_batch(XT, Y, ratios, n=n, row_mask=M, opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = pkg.stats_to_numpy(res["stats"])
+        ok = int((st["status"] == 0).sum())
+        ms = e0.elapsed_time(e1)
+        out[name] = {"solves_per_s": ok / (ms / 1e3), "certified": ok, "solves": B * T, "ms": ms}
+        del res
+    # plain: lasso_path per problem on its gathered rows (X restricted, ld a multiple of 4)
+    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"])
+    tot_ms, tot_ok = 0.0, 0
+    for b in range(-1, sample):
+        bb = max(b, 0)
+        rows = np.nonzero(w["row_mask"][bb])[0]
+        m = rows.size
+        ld = (m + 3) // 4 * 4
+        Xb = torch.zeros((p, ld), dtype=torch.float32, device=dev)
+        Xb[:, :m] = XT[:, torch.from_numpy(rows).to(dev)]
+        yb = torch.from_numpy(np.ascontiguousarray(w["Y"][bb, rows])).to(dev)
+        flush.fill_(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = pkg.solve_path(Xb, yb, ratios, n=m, opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if b >= 0:  # b = -1 is the untimed warm-up
+            st = pkg.stats_to_numpy(res["stats"])
+            tot_ok += int((st["status"] == 0).sum())
+            tot_ms += e0.elapsed_time(e1)
+    out["plain_single_path"] = {"solves_per_s": tot_ok / (tot_ms / 1e3), "certified": tot_ok,
+                                "solves": sample * T, "ms": tot_ms,
+                                "sample": f"first {sample} of the {B} problems, one lasso_path call each"}
+    best = max(out["batched_fp32"]["solves_per_s"], out["batched_split_bf16_tc"]["solves_per_s"])
+    out["tuned_over_plain"] = best / out["plain_single_path"]["solves_per_s"]
+    out["note"] = ("tuned = batched persistent CD (one CTA per problem) with the tensor-core split-BF16 first "
+                   "check or FP32 checks, best of the two; plain = the single-problem path")
+    return out
+
+
+def _learned(pkg, torch, dev, stream, n_train, epochs=20, lr=1e-2, n_eval=1024):
+    """Learned warm start on the fixed 300 x 10000 design at lambda =
+    lambda_max / 20: solver solutions of n_train responses train the 8-layer
+    net (hand-written forward/backward/Adam kernels); held-out responses are
+    then solved from the zero start and from the net's beta0."""
+    import numpy as np
+    import gen
+    w = gen.workload4()
+    n, p = w["n"], w["p"]
+    XT = torch.from_numpy(w["XT"]).to(dev)
+    ratio = torch.tensor([w["lambda_ratio"]], dtype=torch.float64, device=dev)
+    opts = pkg.lasso_default_opts(gemm_dtype=pkg.LASSO_F32)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    Ytr = torch.from_numpy(w["sample"](n_train, 1)).to(dev)
+    Yev = torch.from_numpy(w["sample"](n_eval, 2)).to(dev)
+    tr, ms_gen = timed(lambda: pkg.solve_batch(XT, Ytr, ratio, n=n, opts=opts))
+    net = pkg.ListaNet(XT, n, L=8, ratio=w["lambda_ratio"])
+    Ytil, s = net.normalize(Ytr)
+    tgt = net.targets(tr["beta"][:, 0, :].contiguous(), s)
+    del tr
+    hist, ms_train = timed(lambda: net.fit(Ytil, tgt, epochs=epochs, batch=256, lr=lr, seed=7))
+    pkg.solve_batch(XT, Yev[:8].contiguous(), ratio, n=n, opts=opts)
+    z, ms_zero = timed(lambda: pkg.solve_batch(XT, Yev, ratio, n=n, opts=opts))
+    b0, ms_net = timed(lambda: net.warm_start(Yev))
+    wres, ms_warm = timed(lambda: pkg.solve_batch(XT, Yev, ratio, n=n, beta0=b0, opts=opts))
+    s0 = pkg.stats_to_numpy(z["stats"])
+    s1 = pkg.stats_to_numpy(wres["stats"])
+    bz = z["beta"][:, 0, :]
+    rel = (torch.linalg.norm(b0 - bz, dim=1) / torch.linalg.norm(bz, dim=1).clamp_min(1e-300)).cpu().numpy()
+    return {"workload": w["name"] + ": Gaussian 300x10000 FP32, k~U{5..50}, SNR~U[2,10], lambda=lambda_max/20",
+            "n_train": n_train, "n_eval": n_eval, "epochs": epochs, "lr_relative": lr,
+            "ms_generate_targets": ms_gen, "ms_train": ms_train, "loss_first_epoch": hist[0],
+            "loss_last_epoch": hist[-1],
+            "zero_start": {"solves_per_s": int((s0["status"] == 0).sum()) / (ms_zero / 1e3), "ms": ms_zero,
+                           "mean_passes": float(s0["epochs"].mean()), "x_columns": int(s0["x_columns"].sum())},
+            "learned_start": {"solves_per_s": int((s1["status"] == 0).sum()) / ((ms_warm + ms_net) / 1e3),
+                              "ms": ms_warm, "ms_net": ms_net, "mean_passes": float(s1["epochs"].mean()),
+                              "x_columns": int(s1["x_columns"].sum())},
+            "beta0_rel_err_median": float(np.median(rel))}
 
 
 def main():

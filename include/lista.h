@@ -108,10 +108,16 @@ lasso_status lista_targets(const double* beta_hat, int64_t ldbh, const float* s,
 
 /* Inference: beta0_b = s_b * beta^L(ytil_b) for B responses Y (FP64, row b at
  * Y + b*ldy), written as FP64 rows of beta0 (leading dimension ldb0 >= p):
- * the layout lasso_batch takes as its starting points. */
+ * the layout lasso_batch takes as its starting points.
+ * max_nonzeros > 0 keeps, per row, only the entries whose magnitude is among
+ * the max_nonzeros largest (ties at the cut are all dropped) and sets the
+ * rest to 0: a Lasso solution in general position has at most n nonzeros, and
+ * coordinate descent pays per pass for every nonzero of its iterate, so a
+ * dense start costs more than it saves.  max_nonzeros <= 0 keeps all. */
 lasso_status lista_warm_start(const float* X, int64_t n, int64_t p, int64_t ldx, const float* W, const float* D,
                               const float* tau, int32_t L, const double* Y, int64_t ldy, int64_t B, double* beta0,
-                              int64_t ldb0, void* workspace, size_t workspace_bytes, void* stream);
+                              int64_t ldb0, int64_t max_nonzeros, void* workspace, size_t workspace_bytes,
+                              void* stream);
 
 #ifdef __cplusplus
 }

@@ -172,14 +172,16 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Stage this thread's granules of column j into ring slot s (no-op past nc).
-template <int NGC, bool XLO, typename Ctx>
+// The chain runs on the first CW warps; granule g = tid + 32 CW k.
+template <int NGC, int CW, bool XLO, typename Ctx>
 __device__ __forceinline__ void stage_column(const Ctx& a, float4* ring, int s, int j) {
+  constexpr int CT = 32 * CW;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < NGC; ++k) {
-    const int g = tid + kChainThreads * k;
+    const int g = tid + CT * k;
     if (g < a.ld4) {
-      float4* dst = ring + ((size_t)(s * NGC + k) * kChainThreads + tid) * (XLO ? 2 : 1);
+      float4* dst = ring + ((size_t)(s * NGC + k) * CT + tid) * (XLO ? 2 : 1);
       cp_async16(dst, a.Xh + (long long)j * a.ldx + 4 * g);
       if (XLO) cp_async16(dst + 1, a.Xl + (long long)j * a.ldx + 4 * g);
     }
@@ -187,15 +189,19 @@ __device__ __forceinline__ void stage_column(const Ctx& a, float4* ring, int s, 
 }
 
 // Coordinate updates for chain entries c = 0..nc-1 (positions into A), in
-// order.  rho is held by the 128 chain threads (granules t + 128 k); each of
-// them stages its own granules of the next kRing columns with cp.async, so
-// no cross-thread handshake is needed for the column data.  The only
-// cross-thread step per entry is the exact limb reduction of x_j^T rho.
-// Writes the new coefficients to bdf, the old ones to oldb and the residual
-// after entry c to snapshot c + 1.
-template <int NGC, bool XLO, typename Ctx>
+// order.  rho is held by the 32 CW chain threads (granules t + 32 CW k); each
+// of them stages its own granules of the next kRing columns with cp.async,
+// so no cross-thread handshake is needed for the column data.  The only
+// cross-thread step per entry is the exact limb reduction of x_j^T rho: one
+// redux per limb when the chain is a single warp, plus a named barrier and a
+// shared-memory exchange between warps otherwise.  Writes the new
+// coefficients to bdf, the old ones to oldb and the residual after entry c to
+// snapshot c + 1.
+template <int NGC, int CW, bool XLO, typename Ctx>
 __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, int nc, float rho_bound,
                           float4 (&rh)[NGC], float4 (&rl)[NGC], uint32_t row_bits = 0xffffffffu) {
+  static_assert(CW >= 1 && CW <= kChainWarps, "chain warps");
+  constexpr int CT = 32 * CW;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (nc <= 0) return;
   // records and the feature list of this round
@@ -210,11 +216,11 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
     jl[c] = j;
   }
   __syncthreads();
-  if (warp < kChainWarps) {
+  if (warp < CW) {
     // prologue: stage the first kRing columns, fetch the first two records
 #pragma unroll
     for (int s = 0; s < kRing; ++s) {
-      if (s < nc) stage_column<NGC, XLO>(a, ring, s, jl[s]);
+      if (s < nc) stage_column<NGC, CW, XLO>(a, ring, s, jl[s]);
       cp_async_commit();
     }
     ChainRec r0 = a.recs[0];
@@ -225,31 +231,34 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
       const int slot = e % kRing;
       cp_async_wait<kRing - 1>();  // this thread's copies for entry e have landed
       float4 xs[NGC], xls[NGC];
-      float S0 = 0.f, C0 = 0.f, S1 = 0.f, C1 = 0.f;
+      // compensated accumulators: two when a lane holds one granule (fewer
+      // limb conversions), four (one per float4 component) for longer dots
+      constexpr bool kFour = NGC >= 2;
+      float S0 = 0.f, C0 = 0.f, S1 = 0.f, C1 = 0.f, S2 = 0.f, C2 = 0.f, S3 = 0.f, C3 = 0.f;
 #pragma unroll
       for (int k = 0; k < NGC; ++k) {
-        const int g = tid + kChainThreads * k;
+        const int g = tid + CT * k;
         xs[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         xls[k] = xs[k];
         if (g < a.ld4) {
-          const float4* src = ring + ((size_t)(slot * NGC + k) * kChainThreads + tid) * (XLO ? 2 : 1);
+          const float4* src = ring + ((size_t)(slot * NGC + k) * CT + tid) * (XLO ? 2 : 1);
           xs[k] = mask_bits(mask_rows(src[0], g, a.n), row_bits >> (4 * k));
           if (XLO) {
             xls[k] = mask_bits(mask_rows(src[1], g, a.n), row_bits >> (4 * k));
             dot2_acc2(xs[k].x, xls[k].x, rh[k].x, rl[k].x, S0, C0);
             dot2_acc2(xs[k].y, xls[k].y, rh[k].y, rl[k].y, S1, C1);
-            dot2_acc2(xs[k].z, xls[k].z, rh[k].z, rl[k].z, S0, C0);
-            dot2_acc2(xs[k].w, xls[k].w, rh[k].w, rl[k].w, S1, C1);
+            dot2_acc2(xs[k].z, xls[k].z, rh[k].z, rl[k].z, kFour ? S2 : S0, kFour ? C2 : C0);
+            dot2_acc2(xs[k].w, xls[k].w, rh[k].w, rl[k].w, kFour ? S3 : S1, kFour ? C3 : C1);
           } else {
             dot2_acc(xs[k].x, rh[k].x, rl[k].x, S0, C0);
             dot2_acc(xs[k].y, rh[k].y, rl[k].y, S1, C1);
-            dot2_acc(xs[k].z, rh[k].z, rl[k].z, S0, C0);
-            dot2_acc(xs[k].w, rh[k].w, rl[k].w, S1, C1);
+            dot2_acc(xs[k].z, rh[k].z, rl[k].z, kFour ? S2 : S0, kFour ? C2 : C0);
+            dot2_acc(xs[k].w, rh[k].w, rl[k].w, kFour ? S3 : S1, kFour ? C3 : C1);
           }
         }
       }
       // refill the slot just read with entry e + kRing (always commit a group)
-      if (e + kRing < nc) stage_column<NGC, XLO>(a, ring, slot, jl[e + kRing]);
+      if (e + kRing < nc) stage_column<NGC, CW, XLO>(a, ring, slot, jl[e + kRing]);
       cp_async_commit();
       const ChainRec r2 = (e + 2 < nc) ? a.recs[e + 2] : r1;  // prefetch
       // |partial sums| <= ||x_j|| ||rho|| <= nf * rho_bound
@@ -257,12 +266,21 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
       limb_scale(2.0f * r0.nf * rho_bound + 1e-30f, sc, isc);
       limbs3 L = limbs_add(limbs_add(to_limbs(S0, sc), to_limbs(C0, sc)),
                            limbs_add(to_limbs(S1, sc), to_limbs(C1, sc)));
+      if (kFour)
+        L = limbs_add(L, limbs_add(limbs_add(to_limbs(S2, sc), to_limbs(C2, sc)),
+                                   limbs_add(to_limbs(S3, sc), to_limbs(C3, sc))));
+      // carries out of the two low limbs before the cross-thread sum: every
+      // limb is then below 2^22 + 1 in magnitude, and 128 of them fit int32
+      L = limbs_norm(L);
       L = warp_limbs_sum(L);
-      if (lane == 0) cs.red[e & 1][warp] = L;
-      named_bar_sync(1, kChainThreads);
-      limbs3 Tl = cs.red[e & 1][0];
+      limbs3 Tl = L;
+      if (CW > 1) {
+        if (lane == 0) cs.red[e & 1][warp] = L;
+        named_bar_sync(1, CT);
+        Tl = cs.red[e & 1][0];
 #pragma unroll
-      for (int w = 1; w < kChainWarps; ++w) Tl = limbs_add(Tl, cs.red[e & 1][w]);
+        for (int w = 1; w < CW; ++w) Tl = limbs_add(Tl, cs.red[e & 1][w]);
+      }
       const df2 g = limbs_to_df(Tl, isc);
       const df2 beta{r0.b.x, r0.b.y};
       df2 nb, d;
@@ -292,7 +310,7 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
       float* sn = a.snap + (size_t)(e + 1) * 2 * a.ldw;
 #pragma unroll
       for (int k = 0; k < NGC; ++k) {
-        const int gi = tid + kChainThreads * k;
+        const int gi = tid + CT * k;
         if (gi < a.ld4) {
           __stcg(reinterpret_cast<float4*>(sn) + gi, rh[k]);
           __stcg(reinterpret_cast<float4*>(sn + a.ldw) + gi, rl[k]);
@@ -306,30 +324,32 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
   __syncthreads();
 }
 
-// rho planes (global) <-> chain registers of CTA 0 (threads >= 128 hold zeros)
-template <int NGC, typename Ctx>
+// rho planes (global) <-> chain registers of CTA 0 (threads >= 32 CW hold zeros)
+template <int NGC, int CW, typename Ctx>
 __device__ __forceinline__ void load_rho_regs(const Ctx& a, const float* h, const float* l, float4 (&rh)[NGC],
                                               float4 (&rl)[NGC]) {
+  constexpr int CT = 32 * CW;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < NGC; ++k) {
-    const int g = tid + kChainThreads * k;
+    const int g = tid + CT * k;
     rh[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     rl[k] = rh[k];
-    if (tid < kChainThreads && g < a.ld4) {
+    if (tid < CT && g < a.ld4) {
       rh[k] = ldcg4(h, g);
       rl[k] = ldcg4(l, g);
     }
   }
 }
-template <int NGC, typename Ctx>
+template <int NGC, int CW, typename Ctx>
 __device__ __forceinline__ void store_rho_regs(const Ctx& a, float* h, float* l, const float4 (&rh)[NGC],
                                                const float4 (&rl)[NGC]) {
+  constexpr int CT = 32 * CW;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < NGC; ++k) {
-    const int g = tid + kChainThreads * k;
-    if (tid < kChainThreads && g < a.ld4) {
+    const int g = tid + CT * k;
+    if (tid < CT && g < a.ld4) {
       __stcg(reinterpret_cast<float4*>(h) + g, rh[k]);
       __stcg(reinterpret_cast<float4*>(l) + g, rl[k]);
     }

@@ -150,6 +150,17 @@ __device__ __forceinline__ limbs3 to_limbs(float v, float scale) {
 
 __device__ __forceinline__ limbs3 limbs_add(limbs3 x, limbs3 y) { return limbs3{x.a + y.a, x.b + y.b, x.c + y.c}; }
 
+// the same value with carries moved up: |b|, |c| <= 2^22 afterwards
+__device__ __forceinline__ limbs3 limbs_norm(limbs3 L) {
+  const int cc = (L.c + (1 << 22)) >> 23;
+  L.c -= cc << 23;
+  L.b += cc;
+  const int cb = (L.b + (1 << 22)) >> 23;
+  L.b -= cb << 23;
+  L.a += cb;
+  return L;
+}
+
 __device__ __forceinline__ limbs3 warp_limbs_sum(limbs3 L) {
   return limbs3{__reduce_add_sync(0xffffffffu, L.a), __reduce_add_sync(0xffffffffu, L.b),
                 __reduce_add_sync(0xffffffffu, L.c)};

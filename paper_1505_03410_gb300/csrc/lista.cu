@@ -354,11 +354,41 @@ __global__ void targets_kernel(const double* bh, long long ldbh, const float* s,
   }
 }
 
-__global__ void unscale_kernel(const float* betaL, const float* s, int B, int p, double* out, long long ldo) {
-  const size_t MN = (size_t)p * B;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(e / p), j = (int)(e % p);
-    out[(size_t)b * ldo + j] = (double)s[b] * (double)betaL[e];
+// One block per row: beta0 = s_b * beta^L, keeping only entries whose
+// magnitude is among the K largest of the row (K <= 0: all).  The cut is the
+// smallest t (as the bit pattern of a non-negative float, whose order is the
+// order of the values) with #{|beta_j| >= t} <= K, found by bisection over
+// the 31 magnitude bits; entries below t are set to 0.
+__global__ void unscale_kernel(const float* betaL, const float* s, int p, long long K, double* out, long long ldo) {
+  __shared__ int red[kEwThreads / 32];
+  __shared__ unsigned cut;
+  const int b = blockIdx.x;
+  const float* row = betaL + (size_t)b * p;
+  if (threadIdx.x == 0) cut = 0u;
+  __syncthreads();
+  if (K > 0 && K < p) {
+    unsigned lo = 0u, hi = 0x7f800000u;  // #{>= hi} = 0 <= K (finite entries)
+    while (lo < hi) {
+      const unsigned mid = lo + ((hi - lo) >> 1);
+      int cnt = 0;
+      for (int j = threadIdx.x; j < p; j += blockDim.x) cnt += (__float_as_uint(fabsf(row[j])) >= mid) ? 1 : 0;
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cnt;
+      __syncthreads();
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += red[w];
+      if ((long long)tot <= K) hi = mid;
+      else lo = mid + 1;
+    }
+    if (threadIdx.x == 0) cut = hi;
+    __syncthreads();
+  }
+  const unsigned t = cut;
+  const double sb = (double)s[b];
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const float v = row[j];
+    out[(size_t)b * ldo + j] = (__float_as_uint(fabsf(v)) >= t) ? sb * (double)v : 0.0;
   }
 }
 
@@ -699,7 +729,7 @@ lasso_status lista_targets(const double* beta_hat, int64_t ldbh, const float* s,
 
 lasso_status lista_warm_start(const float* X, int64_t n, int64_t p, int64_t ldx, const float* W, const float* D,
                               const float* tau, int32_t L, const double* Y, int64_t ldy, int64_t B, double* beta0,
-                              int64_t ldb0, void* ws, size_t ws_bytes, void* stream) {
+                              int64_t ldb0, int64_t max_nonzeros, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
   lasso_status r = check_sizes("lista_warm_start", n, p, L, B);
   if (r != LASSO_OK) return r;
@@ -713,7 +743,7 @@ lasso_status lista_warm_start(const float* X, int64_t n, int64_t p, int64_t ldx,
   if ((r = normalize_impl(X, n, p, ldx, Y, ldy, B, yt, n, s, w, ws, st)) != LASSO_OK) return r;
   float* bl = at<float>(ws, w.g);
   if ((r = forward_impl(X, n, p, ldx, W, D, tau, L, yt, n, B, bl, false, w, ws, st)) != LASSO_OK) return r;
-  unscale_kernel<<<ew_blocks((size_t)B * p), kEwThreads, 0, st>>>(bl, s, (int)B, (int)p, beta0, ldb0);
+  unscale_kernel<<<(unsigned)B, kEwThreads, 0, st>>>(bl, s, (int)p, (long long)max_nonzeros, beta0, ldb0);
   CUDA_TRY(cudaGetLastError());
   return LASSO_OK;
 }

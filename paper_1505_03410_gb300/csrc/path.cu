@@ -58,6 +58,7 @@ struct Ctrl {
   // cycle counters of CTA 0 by phase (check, chain, verify, rollback/accept,
   // end of pass, setup of a round) and event counts (rounds, rollbacks)
   unsigned long long prof[8];
+  int win;                    // positions a round may span (adaptive, see the passes)
 };
 
 struct Args {
@@ -126,7 +127,7 @@ __device__ __forceinline__ int slice_begin(const Args& a, int c) {
 
 // Row bits of the chain thread's granules for problem b: bit 4k + c is set
 // when row 4 (tid + 128 k) + c belongs to the problem's row subset.
-template <int NGC>
+template <int NGC, int CW>
 __device__ __forceinline__ uint32_t chain_row_bits(const Args& a, int b) {
   const int tid = threadIdx.x;
   uint32_t bits = 0;
@@ -134,7 +135,7 @@ __device__ __forceinline__ uint32_t chain_row_bits(const Args& a, int b) {
   for (int k = 0; k < NGC; ++k)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int row = 4 * (tid + kChainThreads * k) + c;
+      const int row = 4 * (tid + 32 * CW * k) + c;
       const bool in = row < a.n && (a.rmask == nullptr || a.rmask[row + (size_t)b * a.ldm] != 0);
       bits |= (in ? 1u : 0u) << (4 * k + c);
     }
@@ -289,9 +290,10 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
 // BATCH = false: the whole grid cooperates on one problem (grid barriers).
 // BATCH = true: every CTA is a one-CTA "grid" with its own workspace copy and
 // solves problems taken from a queue, one whole path at a time.
-template <int NGC, bool XLO, bool BATCH>
+template <int NGC, int CW, bool XLO, bool BATCH>
 __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
-  constexpr int NG = 4 * NGC;  // float4 granules per lane in warp-wide dots
+  constexpr int NG = CW * NGC;  // float4 granules per lane in warp-wide dots
+  constexpr int CT = 32 * CW;   // chain threads (the first CW warps of CTA 0)
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ ChainSmem cs;
   __shared__ double dbuf[32];
@@ -308,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
   // mask words of the slice: f0 is a multiple of 32 when the slice is not
   // empty; CTAs past the last feature (f0 == f1 == p) own no word
   const int wd0 = f0 >> 5, wd1 = f1 > f0 ? (f1 + 31) >> 5 : wd0;
+  const int win_min = max(64, 4 * G * nwarps);  // smallest round window after a rollback
   ChainCtx cx{a.Xh,          a.Xl,           a.ldx,           a.ldw,          a.n,
                     a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
                     WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap), WS(float, msnap)};
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
     double* bout = a.beta_out + (size_t)b * a.T * a.p;
     uint32_t* mout = a.mask_out ? a.mask_out + (size_t)b * a.T * a.words : nullptr;
     lasso_path_stats* sout = a.stats + (size_t)b * a.T;
-    const uint32_t rbits = BATCH ? chain_row_bits<NGC>(a, b) : 0xffffffffu;
+    const uint32_t rbits = BATCH ? chain_row_bits<NGC, CW>(a, b) : 0xffffffffu;
     if (vload(*err) != 0) goto fail;  // NaN/Inf input or lambda_max = 0
 
   const int t_begin = (BATCH && a.lockstep) ? a.t0 : 0, t_end = (BATCH && a.lockstep) ? a.t1 : a.T;
@@ -699,6 +702,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
         ctl->s = tots;
         ctl->nzl = totz;
         ctl->mcur = 0.f;
+        ctl->win = totk;
       }
       scope_n = a.xtr_scope == 0 ? a.p : totk;
       GSYNC();
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
           // residual shares of the coefficients removed by the check, ascending j
           const int nz = vload(ctl->nzl);
           if (nz > 0) {
-            load_rho_regs<NGC>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
+            load_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             for (int i = 0; i < nz; ++i) {
               const int jj = __ldcg(WS(int, zl_j) + i);
               const df2 d = df_from_double(-__ldcg(WS(double, zl_b) + jj));  // rho -= (0 - b) x_j
@@ -721,8 +725,8 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
               const float* coll = XLO ? a.Xl + (long long)jj * a.ldx : nullptr;
 #pragma unroll
               for (int k = 0; k < NGC; ++k) {
-                const int g = tid + kChainThreads * k;
-                if (tid < kChainThreads && g < a.ld4) {
+                const int g = tid + CT * k;
+                if (tid < CT && g < a.ld4) {
                   const float4 x = mask_bits(ld_x4(col, g, a.n), rbits >> (4 * k));
                   if (XLO) {
                     const float4 xl = mask_bits(ld_x4(coll, g, a.n), rbits >> (4 * k));
@@ -739,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
                 }
               }
             }
-            store_rho_regs<NGC>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
+            store_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             __syncthreads();
             if (tid == 0) {
               float mv = ctl->mcur;
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
         for (int e = 0; e < a.f && epochs < a.max_epochs; ++e) {
           // ---- one pass over the safe-active list, in rounds
           if (cta == 0) {
-            load_rho_regs<NGC>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
+            load_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             if (tid == 0) {
               ctl->pos = 0;
               ctl->sup_idx = 0;
@@ -767,12 +771,18 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
           }
           for (;;) {
             PROF(7);
-            // R1 (CTA 0): chain = [forced entry] + next support positions (at most s_cap)
+            // R1 (CTA 0): chain = [forced entry] + the support positions of the
+            // round's window [pos, pos + win) (at most s_cap of them).  The round
+            // ends at the window's end, or at the first support position left out.
             if (cta == 0) {
               const int si = vload(ctl->sup_idx), forced = vload(ctl->forced);
-              const int take = min(s - si, a.s_cap - (forced >= 0 ? 1 : 0));
+              const int pos0 = vload(ctl->pos);
+              const int plim = (int)min((long long)q, (long long)pos0 + vload(ctl->win));
+              const int in_win = lower_bound_i(sup + si, s - si, plim);
+              const int take = min(in_win, a.s_cap - (forced >= 0 ? 1 : 0));
               const int nc = take + (forced >= 0 ? 1 : 0);
-              const int rend = (si + take < s) ? __ldcg(sup + si + take) : q;
+              const int next = (si + take < s) ? __ldcg(sup + si + take) : q;
+              const int rend = take < in_win ? next : min(plim, next);
               for (int c = tid; c < nc; c += kThreads)
                 WS(int, chain)[c] = (forced >= 0) ? (c == 0 ? forced : __ldcg(sup + si + c - 1)) : __ldcg(sup + si + c);
               __syncthreads();
@@ -784,9 +794,9 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
                 ctl->fstar = kNoPos;
                 WS(float, msnap)[0] = ctl->mcur;
               }
-              store_rho_regs<NGC>(cx, WS(float, snap), WS(float, snap) + a.ldw, rh, rl);  // snapshot 0
+              store_rho_regs<NGC, CW>(cx, WS(float, snap), WS(float, snap) + a.ldw, rh, rl);  // snapshot 0
               __syncthreads();
-              run_chain<NGC, XLO>(cx, cs, ring, jl, nc, rb, rh, rl, rbits);
+              run_chain<NGC, CW, XLO>(cx, cs, ring, jl, nc, rb, rh, rl, rbits);
               __threadfence();
               if (prof_thread) ctl->prof[5] += (unsigned long long)nc;
             }
@@ -885,6 +895,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
                   ctl->pos = rend;
                   ctl->forced = -1;
                   ctl->done = rend >= q ? 1 : 0;
+                  ctl->win = (int)min((long long)q, 2ll * vload(ctl->win));
                 }
               } else {
                 // chain entries before the entering position stand; later ones are undone
@@ -892,7 +903,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
                 const int seg = lower_bound_i(WS(int, chain), nc, fst);
                 for (int c = seg + tid; c < nc; c += kThreads) WS(float2, bdf)[__ldcg(WS(int, A) + __ldcg(WS(int, chain) + c))] = WS(float2, oldb)[c];
                 const float* sh = WS(float, snap) + (size_t)seg * 2 * a.ldw;
-                load_rho_regs<NGC>(cx, sh, sh + a.ldw, rh, rl);
+                load_rho_regs<NGC, CW>(cx, sh, sh + a.ldw, rh, rl);
                 __syncthreads();
                 if (tid == 0) {
                   if (forced >= 0) {
@@ -906,6 +917,11 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
                   // movement) <= (2 M_end - M_seg - M_e) + (new movement)
                   const float m_end = __ldcg(WS(float, msnap) + nc), m_seg = __ldcg(WS(float, msnap) + seg);
                   ctl->mcur = __fsub_ru(__fmul_ru(2.0f, m_end), m_seg);
+                  // the verification beyond fst was spent on an undone branch: the
+                  // next window is twice the span this round kept, and at least
+                  // four positions per warp of the grid
+                  const int pos_r = vload(ctl->pos);
+                  ctl->win = max(win_min, 2 * (fst - pos_r));
                   ctl->sup_idx = si + seg - (forced >= 0 ? 1 : 0);
                   ctl->forced = fst;
                   ctl->pos = fst;
@@ -922,7 +938,7 @@ __global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
           // end of pass (CTA 0): write rho; next support list = survivors of the
           // old list merged with the entered positions (both ascending)
           if (cta == 0) {
-            store_rho_regs<NGC>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
+            store_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             const int ne = vload(ctl->n_entered);
             __syncthreads();
             int nsurv = 0;
@@ -1267,18 +1283,35 @@ void set_offsets(Args& a, const Layout& L) {
   a.s_cap = L.s_cap;
 }
 
-template <int NGC, bool XLO, bool BATCH>
+template <int NGC, int CW, bool XLO, bool BATCH>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&path_kernel<NGC, XLO, BATCH>);
+  return reinterpret_cast<const void*>(&path_kernel<NGC, CW, XLO, BATCH>);
 }
 
-const void* pick_kernel(int ngc, bool xlo, bool batch) {
-  if (batch) return ngc == 1 ? kernel_ptr<1, false, true>() : ngc == 2 ? kernel_ptr<2, false, true>()
-                                                                        : kernel_ptr<4, false, true>();
-  if (xlo) return ngc == 1 ? kernel_ptr<1, true, false>() : ngc == 2 ? kernel_ptr<2, true, false>()
-                                                                      : kernel_ptr<4, true, false>();
-  return ngc == 1 ? kernel_ptr<1, false, false>() : ngc == 2 ? kernel_ptr<2, false, false>()
-                                                             : kernel_ptr<4, false, false>();
+// Chain shape for n rows.  A coordinate step is one warp's dependent
+// instruction stream, so the chain spreads the rows until every lane holds a
+// single float4 granule: one warp (no barrier, no shared-memory exchange)
+// while n <= 128, four warps and 1, 2 or 4 granules per lane above.  Measured
+// on the 500-row path: one warp with four granules per lane was 1.57x slower
+// than four warps with one.
+struct ChainShape {
+  int cw, ngc;
+};
+
+ChainShape chain_shape(int64_t n, bool batch) {
+  const int ld4 = (int)((n + 3) / 4);
+  if (!batch && ld4 <= 32) return ChainShape{1, 1};
+  return ChainShape{4, ld4 <= 128 ? 1 : (ld4 <= 256 ? 2 : 4)};
+}
+
+const void* pick_kernel(ChainShape c, bool xlo, bool batch) {
+  if (batch) return c.ngc == 1 ? kernel_ptr<1, 4, false, true>()
+                  : c.ngc == 2 ? kernel_ptr<2, 4, false, true>() : kernel_ptr<4, 4, false, true>();
+  if (c.cw == 1) return xlo ? kernel_ptr<1, 1, true, false>() : kernel_ptr<1, 1, false, false>();
+  if (xlo) return c.ngc == 1 ? kernel_ptr<1, 4, true, false>()
+                  : c.ngc == 2 ? kernel_ptr<2, 4, true, false>() : kernel_ptr<4, 4, true, false>();
+  return c.ngc == 1 ? kernel_ptr<1, 4, false, false>()
+         : c.ngc == 2 ? kernel_ptr<2, 4, false, false>() : kernel_ptr<4, 4, false, false>();
 }
 
 void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) {
@@ -1297,9 +1330,9 @@ void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) 
 
 // dynamic shared memory of a CTA: the feature list of a round and the ring
 // of kRing staged columns (each chain thread's granules, two planes for FP64)
-size_t dyn_smem(int s_cap, int ngc, bool xlo) {
+size_t dyn_smem(int s_cap, ChainShape c, bool xlo) {
   const size_t jl_bytes = (((size_t)(s_cap + 1) * sizeof(int)) + 127) & ~(size_t)127;
-  return jl_bytes + (size_t)kRing * ngc * kChainThreads * 16 * (xlo ? 2 : 1);
+  return jl_bytes + (size_t)kRing * c.ngc * 32 * c.cw * 16 * (xlo ? 2 : 1);
 }
 
 struct DevInfo {
@@ -1313,11 +1346,6 @@ lasso_status dev_info(DevInfo& d) {
   CUDA_TRY(cudaDeviceGetAttribute(&d.coop, cudaDevAttrCooperativeLaunch, dev));
   CUDA_TRY(cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   return LASSO_OK;
-}
-
-int ngc_for(int64_t n) {
-  const int ld4 = (int)((n + 3) / 4);
-  return (ld4 <= 128) ? 1 : (ld4 <= 256 ? 2 : 4);
 }
 
 // resident CTAs of the batched solver for a given device (fixed, so that the
@@ -1368,13 +1396,13 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
     a.ldx = ldx;
   }
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + a.o_ctrl);
-  const int ngc = ngc_for(n);
-  const void* kfn = pick_kernel(ngc, f64, false);
+  const ChainShape cs = chain_shape(n, false);
+  const void* kfn = pick_kernel(cs, f64, false);
   DevInfo d{};
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
   if (!d.coop) return set_error(LASSO_ERR_CUDA, "device does not support cooperative launch");
-  const size_t dyn = dyn_smem(L.s_cap, ngc, f64);
+  const size_t dyn = dyn_smem(L.s_cap, cs, f64);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
   CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
@@ -1504,9 +1532,9 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   a.Xl = nullptr;
   a.ldx = ldx;
   a.fs = (int)((p + 31) / 32 * 32);
-  const int ngc = ngc_for(n);
-  const void* kfn = pick_kernel(ngc, false, true);
-  const size_t dyn = dyn_smem(bl.L.s_cap, ngc, false);
+  const ChainShape cs = chain_shape(n, true);
+  const void* kfn = pick_kernel(cs, false, true);
+  const size_t dyn = dyn_smem(bl.L.s_cap, cs, false);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
   CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));

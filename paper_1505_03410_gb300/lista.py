@@ -35,7 +35,7 @@ def _lib():
         lib.lista_adam.argtypes = [V, V, V, V, I64, I32, F, F, F, F, V]
         lib.lista_gather.argtypes = [V, I64, V, I64, I64, V, I64, V]
         lib.lista_targets.argtypes = [V, I64, V, I64, I64, V, V]
-        lib.lista_warm_start.argtypes = [V, I64, I64, I64, V, V, V, I32, V, I64, I64, V, I64, V, SZ, V]
+        lib.lista_warm_start.argtypes = [V, I64, I64, I64, V, V, V, I32, V, I64, I64, V, I64, I64, V, SZ, V]
         for name in EXPORTED[1:]:
             getattr(lib, name).restype = ctypes.c_int
         _bound = True
@@ -96,10 +96,11 @@ def lista_targets(beta_hat, ldbh, s, B, p, targets, stream):
                                            _vp(stream)))
 
 
-def lista_warm_start(X, n, p, ldx, W, D, tau, L, Y, ldy, B, beta0, ldb0, workspace, workspace_bytes, stream):
+def lista_warm_start(X, n, p, ldx, W, D, tau, L, Y, ldy, B, beta0, ldb0, max_nonzeros, workspace, workspace_bytes,
+                     stream):
     return _lg._check(_lib().lista_warm_start(_vp(X), int(n), int(p), int(ldx), _vp(W), _vp(D), _vp(tau), int(L),
-                                              _vp(Y), int(ldy), int(B), _vp(beta0), int(ldb0), _vp(workspace),
-                                              int(workspace_bytes), _vp(stream)))
+                                              _vp(Y), int(ldy), int(B), _vp(beta0), int(ldb0), int(max_nonzeros),
+                                              _vp(workspace), int(workspace_bytes), _vp(stream)))
 
 
 class ListaNet:
@@ -245,14 +246,16 @@ class ListaNet:
         lista_targets(beta_hat.data_ptr(), ldbh, s.data_ptr(), B, self.p, t.data_ptr(), self._stream())
         return t
 
-    def warm_start(self, Y):
+    def warm_start(self, Y, max_nonzeros=None):
         """beta0 (B, p) float64 for responses Y (B, ldy) float64: the starting
-        points lasso_batch takes."""
+        points lasso_batch takes, each row cut to its max_nonzeros largest
+        entries (default n; 0 keeps all)."""
         import torch
         B, ldy = Y.shape
+        K = self.n if max_nonzeros is None else int(max_nonzeros)
         beta0 = torch.empty((B, self.p), dtype=torch.float64, device=Y.device)
         ws = self.workspace(B)
         lista_warm_start(self.XT.data_ptr(), self.n, self.p, self.ldx, self.W.data_ptr(), self.D.data_ptr(),
-                         self.tau.data_ptr(), self.L, Y.data_ptr(), ldy, B, beta0.data_ptr(), self.p, ws.data_ptr(),
-                         ws.numel(), self._stream())
+                         self.tau.data_ptr(), self.L, Y.data_ptr(), ldy, B, beta0.data_ptr(), self.p, K,
+                         ws.data_ptr(), ws.numel(), self._stream())
         return beta0

@@ -149,3 +149,53 @@ def test_batch_beta0(pkg, gemm, warm):
     g = run_gpu_batch(pkg, prob["XT"], 150, Y, rmask, ratios, beta0=beta0, gemm_dtype=gemm, **opt)
     o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=150, beta0=beta0, **opt)
     check_batch(g, o)
+
+
+def test_batch_captured_in_cuda_graph(pkg):
+    """The lockstep solver allocates nothing and never waits on the host, so
+    a whole lasso_batch call (per lambda: residual packing, tensor-core
+    product, solver launch) can be captured in a CUDA graph once and replayed
+    on new responses; replays equal direct calls."""
+    prob, Y, rmask = _subsample_problem(208, 160, 1400, 12, correlated=True)
+    ratios = oracle.lambda_ratios(10, 2.0)
+    dev = torch.device("cuda:0")
+    opts = pkg.lasso_default_opts(gap_tol_rel=1e-9, gemm_dtype=pkg.LASSO_BF16)
+    Xd = torch.from_numpy(np.ascontiguousarray(prob["XT"], dtype=np.float32)).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    Md = torch.from_numpy(rmask).to(dev)
+    r = torch.from_numpy(ratios).to(dev)
+    B, T, p = Y.shape[0], len(ratios), prob["XT"].shape[0]
+    words = (p + 31) // 32
+    beta = torch.empty((B, T, p), dtype=torch.float64, device=dev)
+    mask = torch.empty((B, T, words), dtype=torch.int32, device=dev)
+    stats = torch.empty(B * T * pkg.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    need = pkg.lasso_batch_workspace_size(160, p, B, opts)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def call(stream):
+        pkg.lasso_batch(Xd.data_ptr(), 160, p, Xd.shape[1], Yd.data_ptr(), Yd.shape[1], Md.data_ptr(), Md.shape[1],
+                        B, r.data_ptr(), T, None, 0, opts, beta.data_ptr(), mask.data_ptr(), stats.data_ptr(),
+                        ws.data_ptr(), need, stream)
+
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        call(side.cuda_stream)  # warm-up outside the capture (lazy module and attribute set-up)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        call(side.cuda_stream)
+    results = []
+    for k in range(2):
+        Yd.copy_(torch.from_numpy(Y * (1.0 + 0.5 * k)))
+        g.replay()
+        torch.cuda.synchronize()
+        gr = dict(beta=beta.cpu().numpy().copy(), mask=mask.cpu().numpy().view(np.uint32).copy(),
+                  stats=pkg.stats_to_numpy(stats).reshape(B, T).copy())
+        direct = run_gpu_batch(pkg, prob["XT"], 160, Y * (1.0 + 0.5 * k), rmask, ratios, gap_tol_rel=1e-9,
+                               gemm_dtype=pkg.LASSO_BF16)
+        np.testing.assert_array_equal(gr["beta"], direct["beta"])
+        np.testing.assert_array_equal(gr["mask"], direct["mask"])
+        np.testing.assert_array_equal(gr["stats"], direct["stats"])
+        results.append(gr)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask * 1.5, ratios, row_mask=rmask, n=160, gap_tol_rel=1e-9)
+    check_batch(results[1], o)

@@ -174,10 +174,21 @@ def test_warm_start_is_scaled_forward(pkg):
     c = _case(407, 50, 700, 4, 33)
     net = _net(pkg, c)
     Yd = torch.from_numpy(c["Y"]).to(DEV)
-    b0 = net.warm_start(Yd).cpu().numpy()
+    b0 = net.warm_start(Yd, max_nonzeros=0).cpu().numpy()
     Ytil, s = net.normalize(Yd)
     out = net.forward(Ytil).cpu().numpy()
     np.testing.assert_allclose(b0, s.cpu().numpy()[:, None].astype(np.float64) * out, rtol=1e-6, atol=0)
+    # the cut to the K largest magnitudes of every row
+    for K in (1, 7, 50, 699):
+        bk = net.warm_start(Yd, max_nonzeros=K).cpu().numpy()
+        for b in range(33):
+            full = b0[b]
+            nz = np.count_nonzero(full)
+            keep = np.abs(full) >= np.sort(np.abs(full))[-K] if K <= nz else full != 0
+            if K < nz and np.sort(np.abs(full))[-K] == np.sort(np.abs(full))[-K - 1]:
+                continue  # a tie at the cut drops all tied entries
+            np.testing.assert_array_equal(bk[b], np.where(keep, full, 0.0))
+            assert np.count_nonzero(bk[b]) <= K
     ref, _ = olista.forward(c["X"], c["W"].astype(np.float64), c["D"].astype(np.float64),
                             c["tau"].astype(np.float64), Ytil.cpu().numpy().astype(np.float64))
     sref = olista.scales(c["X"], c["Y"])
