@@ -66,7 +66,11 @@ typedef struct lasso_opts {
   int32_t gemm_dtype;    /* batched solver: input type of the tensor-core X^T R product at the
                             first check of each lambda (LASSO_BF16 default; LASSO_F32 = exact
                             CUDA-core product); ignored by lasso_path */
-  int32_t reserved[3];   /* must be zero */
+  int32_t batch_ctas_per_sm; /* batched solver: resident CTAs per SM, 1 or 2 (0 = 2, the default).
+                                With 1 the kernel may use up to 255 registers per thread */
+  int32_t gemm_tile_n;   /* lockstep batches: N tile of the tensor-core product, 64, 128 or 256
+                            (0 = 128).  lasso_batch_tune picks these two and gemm_dtype */
+  int32_t reserved;      /* must be zero */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */
@@ -175,6 +179,27 @@ lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, 
                          int32_t T, const double* beta0_dev, int64_t ldb0, const lasso_opts* opts,
                          double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
                          void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Launch-shape autotuner for lasso_batch.  Times every candidate shape
+ * (lasso_batch_tune_candidates() of them: per-CTA FP32 checks or lockstep
+ * split-BF16 products, 1 or 2 solver CTAs per SM, and for lockstep an N tile
+ * of 128 or 256) on the first `sample` problems over the first `lambdas`
+ * ratios of the grid -- a warm-up run, then a run timed with CUDA events on
+ * `stream` -- and writes *opts with the fastest gemm_dtype,
+ * batch_ctas_per_sm and gemm_tile_n to *tuned.  Every candidate makes the
+ * same screening decisions (each equal to the FP64 test's), so the choice
+ * changes the time, not the results.  Arguments as for lasso_batch;
+ * 1 <= sample <= B, 1 <= lambdas <= T; times_ms (host, one float per
+ * candidate) may be NULL.  Synchronises `stream`.  workspace: at least
+ * lasso_batch_tune_workspace_size(n, p, sample, lambdas) bytes, 256-byte
+ * aligned (it also holds the sample's outputs). */
+int32_t lasso_batch_tune_candidates(void);
+size_t lasso_batch_tune_workspace_size(int64_t n, int64_t p, int64_t sample, int32_t lambdas);
+lasso_status lasso_batch_tune(const float* X_dev, int64_t n, int64_t p, int64_t ldx, const double* Y_dev, int64_t ldy,
+                              const uint8_t* row_mask_dev, int64_t ldm, int64_t B, const double* lambda_ratios_dev,
+                              int32_t T, const double* beta0_dev, int64_t ldb0, const lasso_opts* opts, int32_t sample,
+                              int32_t lambdas, lasso_opts* tuned, float* times_ms_host, void* workspace_dev,
+                              size_t workspace_bytes, void* stream);
 
 /* The correlation pass of one GAP SAFE check on its own: c = X^T r and
  * m = ||c||_inf (Eq. (7) needs every |x_j^T rho|, the rescaling of Eq. (8)

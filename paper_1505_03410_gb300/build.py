@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblassogs.so")
-SOURCES = ["api.cu", "path.cu", "static_scratch.cu", "gemm_tc.cu", "lista.cu", "xtr.cu"]
+SOURCES = ["api.cu", "path.cu", "static_scratch.cu", "gemm_tc.cu", "lista.cu", "xtr.cu", "tune.cu"]
 HEADERS = ["dfloat.cuh", "device_util.cuh", "cd_common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -36,8 +36,11 @@ lasso_status check_opts(const lasso_opts& o) {
     return set_error(LASSO_ERR_INVALID_ARG, "gap_tol_rel must be finite and >= 0");
   if (o.gemm_dtype != LASSO_BF16 && o.gemm_dtype != LASSO_F32)
     return set_error(LASSO_ERR_INVALID_ARG, "gemm_dtype must be LASSO_BF16 or LASSO_F32");
-  for (int i = 0; i < 3; ++i)
-    if (o.reserved[i] != 0) return set_error(LASSO_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.batch_ctas_per_sm < 0 || o.batch_ctas_per_sm > 2)
+    return set_error(LASSO_ERR_INVALID_ARG, "batch_ctas_per_sm must be 0, 1 or 2");
+  if (o.gemm_tile_n != 0 && o.gemm_tile_n != 64 && o.gemm_tile_n != 128 && o.gemm_tile_n != 256)
+    return set_error(LASSO_ERR_INVALID_ARG, "gemm_tile_n must be 0, 64, 128 or 256");
+  if (o.reserved != 0) return set_error(LASSO_ERR_INVALID_ARG, "reserved option fields must be zero");
   return LASSO_OK;
 }
 

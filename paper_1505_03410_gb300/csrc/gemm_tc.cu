@@ -225,10 +225,12 @@ lasso_status make_map(CUtensorMap* map, const void* base, int64_t K, int64_t row
 
 }  // namespace
 
-lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, const void* Rb, int64_t ldr,
-                             int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream) {
+namespace {
+
+template <int BN>
+lasso_status launch_bn(const void* Xb, int64_t n, int64_t p, int64_t ldx, const void* Rb, int64_t ldr, int64_t B,
+                       float* C, int64_t ldc, int* err_dev, cudaStream_t stream) {
   CUtensorMap mx, mr;
-  constexpr int BN = 128;
   lasso_status st = make_map(&mx, Xb, n, p, ldx, kBM);
   if (st != LASSO_OK) return st;
   st = make_map(&mr, Rb, n, B, ldr, BN);
@@ -239,6 +241,16 @@ lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, 
   xtr_gemm_kernel<BN><<<grid, kGemmThreads, smem, stream>>>(mx, mr, (int)n, (int)p, (int)B, C, ldc, err_dev);
   CUDA_TRY(cudaGetLastError());
   return LASSO_OK;
+}
+
+}  // namespace
+
+// tile_n: the N tile (64, 128 or 256 accumulator columns of TMEM; 0 = 128)
+lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, const void* Rb, int64_t ldr,
+                             int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream, int tile_n) {
+  if (tile_n == 64) return launch_bn<64>(Xb, n, p, ldx, Rb, ldr, B, C, ldc, err_dev, stream);
+  if (tile_n == 256) return launch_bn<256>(Xb, n, p, ldx, Rb, ldr, B, C, ldc, err_dev, stream);
+  return launch_bn<128>(Xb, n, p, ldx, Rb, ldr, B, C, ldc, err_dev, stream);
 }
 
 }  // namespace lassogs

@@ -22,7 +22,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
 
 size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep);
 lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, const void* Rb, int64_t ldr,
-                             int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream);
+                             int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream, int tile_n = 0);
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
                           const uint8_t* row_mask, int64_t ldm, int64_t B, const double* ratios, int32_t T,
                           const double* beta0, int64_t ldb0, const lasso_opts& o, double* beta_out,

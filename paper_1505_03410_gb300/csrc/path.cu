@@ -290,8 +290,9 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
 // BATCH = false: the whole grid cooperates on one problem (grid barriers).
 // BATCH = true: every CTA is a one-CTA "grid" with its own workspace copy and
 // solves problems taken from a queue, one whole path at a time.
-template <int NGC, int CW, bool XLO, bool BATCH>
-__global__ void __launch_bounds__(kThreads, BATCH ? 2 : 1) path_kernel(Args a) {
+// MINB: CTAs per SM the launch bounds promise (registers per thread <= 65536 / (256 MINB))
+template <int NGC, int CW, bool XLO, bool BATCH, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   constexpr int NG = CW * NGC;  // float4 granules per lane in warp-wide dots
   constexpr int CT = 32 * CW;   // chain threads (the first CW warps of CTA 0)
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -1283,9 +1284,9 @@ void set_offsets(Args& a, const Layout& L) {
   a.s_cap = L.s_cap;
 }
 
-template <int NGC, int CW, bool XLO, bool BATCH>
+template <int NGC, int CW, bool XLO, bool BATCH, int MINB = 1>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&path_kernel<NGC, CW, XLO, BATCH>);
+  return reinterpret_cast<const void*>(&path_kernel<NGC, CW, XLO, BATCH, MINB>);
 }
 
 // Chain shape for n rows.  A coordinate step is one warp's dependent
@@ -1304,9 +1305,11 @@ ChainShape chain_shape(int64_t n, bool batch) {
   return ChainShape{4, ld4 <= 128 ? 1 : (ld4 <= 256 ? 2 : 4)};
 }
 
-const void* pick_kernel(ChainShape c, bool xlo, bool batch) {
-  if (batch) return c.ngc == 1 ? kernel_ptr<1, 4, false, true>()
-                  : c.ngc == 2 ? kernel_ptr<2, 4, false, true>() : kernel_ptr<4, 4, false, true>();
+const void* pick_kernel(ChainShape c, bool xlo, bool batch, int per_sm = 1) {
+  if (batch && per_sm == 2) return c.ngc == 1 ? kernel_ptr<1, 4, false, true, 2>()
+                                 : c.ngc == 2 ? kernel_ptr<2, 4, false, true, 2>() : kernel_ptr<4, 4, false, true, 2>();
+  if (batch) return c.ngc == 1 ? kernel_ptr<1, 4, false, true, 1>()
+                  : c.ngc == 2 ? kernel_ptr<2, 4, false, true, 1>() : kernel_ptr<4, 4, false, true, 1>();
   if (c.cw == 1) return xlo ? kernel_ptr<1, 1, true, false>() : kernel_ptr<1, 1, false, false>();
   if (xlo) return c.ngc == 1 ? kernel_ptr<1, 4, true, false>()
                   : c.ngc == 2 ? kernel_ptr<2, 4, true, false>() : kernel_ptr<4, 4, true, false>();
@@ -1350,8 +1353,8 @@ lasso_status dev_info(DevInfo& d) {
 
 // resident CTAs of the batched solver for a given device (fixed, so that the
 // workspace size does not depend on the occupancy query)
-int batch_grid(int64_t B, int sms) {
-  return (int)std::min<int64_t>(B, std::min<int64_t>((int64_t)sms * 2, kMaxGrid));
+int batch_grid(int64_t B, int sms, int per_sm = 2) {
+  return (int)std::min<int64_t>(B, std::min<int64_t>((int64_t)sms * per_sm, kMaxGrid));
 }
 
 }  // namespace
@@ -1533,7 +1536,9 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   a.ldx = ldx;
   a.fs = (int)((p + 31) / 32 * 32);
   const ChainShape cs = chain_shape(n, true);
-  const void* kfn = pick_kernel(cs, false, true);
+  const int per_sm = o.batch_ctas_per_sm == 1 ? 1 : 2;
+  const int grid = batch_grid(B, d.sms, per_sm);  // <= the regions the layout holds
+  const void* kfn = pick_kernel(cs, false, true, per_sm);
   const size_t dyn = dyn_smem(bl.L.s_cap, cs, false);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
@@ -1542,7 +1547,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
     // each CTA solves whole paths; its first checks are CUDA-core FP32 passes
     CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
     void* params[] = {&a};
-    CUDA_TRY(cudaLaunchKernel(kfn, dim3(bl.grid), dim3(kThreads), params, dyn, stream));
+    CUDA_TRY(cudaLaunchKernel(kfn, dim3(grid), dim3(kThreads), params, dyn, stream));
     return LASSO_OK;
   }
   // lockstep: per lambda, the residuals of all problems -> one tensor-core
@@ -1571,7 +1576,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
                                                    o.warm_start ? a.o_rho_h : a.o_rho0_h, (int)n, (int)B, (int)Lk,
                                                    t == 0 ? 1 : 0, R3);
       CUDA_TRY(cudaGetLastError());
-      st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream);
+      st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream, o.gemm_tile_n);
       if (st != LASSO_OK) return st;
     }
     a.cfirst = use_gemm ? C : nullptr;
@@ -1579,7 +1584,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
     a.t0 = t;
     a.t1 = t + 1;
     void* params[] = {&a};
-    CUDA_TRY(cudaLaunchKernel(kfn, dim3(bl.grid), dim3(kThreads), params, dyn, stream));
+    CUDA_TRY(cudaLaunchKernel(kfn, dim3(grid), dim3(kThreads), params, dyn, stream));
   }
   return LASSO_OK;
 }

@@ -3,27 +3,32 @@
 // |x_j^T rho|, the dual rescaling of Eq. (8) needs the maximum).
 //
 // The pass reads each column once and does 2 flops per 4 bytes: it is bound
-// by HBM bandwidth.  Each warp owns U adjacent columns per step and issues
-// all U * NG float4 loads of them (streaming, evict-first) before it reduces,
-// so every SM keeps enough bytes in flight to cover the DRAM latency; r sits
-// in registers (granule g = lane + 32 k of the warp).  The grid is persistent
-// (CTAs per SM from the occupancy calculator times the SM count) and strides
-// over the column groups.
+// by HBM bandwidth.  Columns stream through shared memory by TMA: in each CTA
+// one producer thread issues 1-D bulk copies (cp.async.bulk, one per column,
+// its first 4 ceil(n/4) floats) of a block of columns into a 4-stage ring
+// guarded by mbarriers, and 8 consumer warps take the columns of a stage one
+// per warp, with r in registers (granule g = lane + 32 k).  The copy engine
+// keeps up to the whole ring (about 96 KB) in flight per CTA without using
+// the SM's outstanding-load slots, which is what limited a load-based
+// version.  Two CTAs per SM, grid = 2 x SMs, each striding over the blocks.
+// Every wait is bounded by the global timer; after a timeout the producer
+// waits (bounded) for its copies in flight before the CTA exits, and the
+// maximum is reported as NaN.
 #include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace lassogs {
 namespace {
 
-constexpr int kXtrThreads = 256;
-
-__device__ __forceinline__ float4 ld_stream4(const float* p) {
-  return __ldcs(reinterpret_cast<const float4*>(p));
-}
+constexpr int kConsumerWarps = 8;
+constexpr int kXtrThreads = (kConsumerWarps + 1) * 32;
+constexpr int kXStages = 4;
+constexpr int kStageTarget = 24576;  // bytes of columns per stage (a whole number of columns)
 
 // rows >= n of the last granule are padding of the caller's buffer: zero them
 __device__ __forceinline__ float4 mask_tail(float4 v, int g, int n) {
@@ -37,83 +42,117 @@ __device__ __forceinline__ float4 mask_tail(float4 v, int g, int n) {
   return v;
 }
 
-template <int NG, int U>
-__global__ void __launch_bounds__(kXtrThreads) xtr_f32_kernel(const float* __restrict__ X, long long ldx, int n, int p,
-                                                              const float* __restrict__ r, float* __restrict__ c,
-                                                              unsigned* __restrict__ cmax_bits) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ld4 = (n + 3) >> 2;
-  float4 r4[NG];
-#pragma unroll
-  for (int k = 0; k < NG; ++k) {
-    const int g = lane + 32 * k;
-    r4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (4 * g + 3 < n) {
-      r4[k] = __ldg(reinterpret_cast<const float4*>(r) + g);
-    } else if (g < ld4) {  // the ragged last granule: only the n entries of r are read
-      const int i = 4 * g;
-      r4[k].x = __ldg(r + i);
-      if (i + 1 < n) r4[k].y = __ldg(r + i + 1);
-      if (i + 2 < n) r4[k].z = __ldg(r + i + 2);
-    }
-  }
-  const long long gw = (long long)blockIdx.x * (kXtrThreads / 32) + warp;
-  const long long nw = (long long)gridDim.x * (kXtrThreads / 32);
-  float mx = 0.f;
-  for (long long j0 = gw * U; j0 < p; j0 += nw * U) {
-    float4 x[U][NG];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long j = j0 + u;
-#pragma unroll
-      for (int k = 0; k < NG; ++k) {
-        const int g = lane + 32 * k;
-        x[u][k] = (j < p && g < ld4) ? ld_stream4(X + j * ldx + 4 * g) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-    }
-    float acc[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      float s = 0.f;
-#pragma unroll
-      for (int k = 0; k < NG; ++k) {
-        const float4 v = mask_tail(x[u][k], lane + 32 * k, n);
-        s = __fmaf_rn(v.x, r4[k].x, s);
-        s = __fmaf_rn(v.y, r4[k].y, s);
-        s = __fmaf_rn(v.z, r4[k].z, s);
-        s = __fmaf_rn(v.w, r4[k].w, s);
-      }
-      acc[u] = s;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[u] = __fadd_rn(acc[u], __shfl_xor_sync(0xffffffffu, acc[u], o));
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long j = j0 + u;
-      if (j < p) {
-        if (lane == u) c[j] = acc[u];
-        mx = fmaxf(mx, fabsf(acc[u]));
-      }
-    }
-  }
-  // the maximum does not depend on the order in which warps report it
-  if (lane == 0 && cmax_bits) atomicMax(cmax_bits, __float_as_uint(mx));
+// wait on an mbarrier phase with only the time limit (used to drain copies
+// in flight after an error, when the error word already says "stop")
+__device__ __forceinline__ void drain_wait(uint64_t* bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return;
 }
 
-template <int NG, int U>
+template <int NG>
+__global__ void __launch_bounds__(kXtrThreads, 2)
+    xtr_f32_kernel(const float* __restrict__ X, long long ldx, int n, int p, int cols_per_stage,
+                   const float* __restrict__ r, float* __restrict__ c, unsigned* __restrict__ cmax_bits) {
+  extern __shared__ __align__(128) unsigned char xsm[];
+  __shared__ __align__(8) uint64_t full[kXStages], empty[kXStages];
+  __shared__ int s_err;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ld4 = (n + 3) >> 2;
+  const unsigned col_bytes = 16u * (unsigned)ld4;
+  const long long nblocks = (p + cols_per_stage - 1) / cols_per_stage;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    s_err = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == kConsumerWarps) {
+    if (lane == 0) {  // producer
+      long long issued = 0;
+      for (long long blk = blockIdx.x; blk < nblocks; blk += gridDim.x, ++issued) {
+        const int s = (int)(issued % kXStages);
+        if (issued >= kXStages && !mbar_wait(&empty[s], (unsigned)(((issued / kXStages) - 1) & 1), &s_err)) break;
+        const long long j0 = blk * cols_per_stage;
+        const int cols = (int)min((long long)cols_per_stage, (long long)p - j0);
+        unsigned char* dst = xsm + (size_t)s * cols_per_stage * col_bytes;
+        mbar_arrive_expect_tx(&full[s], (unsigned)cols * col_bytes);
+        for (int cc = 0; cc < cols; ++cc)
+          bulk_g2s(dst + (size_t)cc * col_bytes, X + (j0 + cc) * ldx, col_bytes, &full[s]);
+      }
+      if (ld_volatile(&s_err) != 0)  // copies still in flight land before the CTA exits
+        for (long long k = max(0ll, issued - kXStages); k < issued; ++k)
+          drain_wait(&full[k % kXStages], (unsigned)((k / kXStages) & 1));
+    }
+  } else {  // consumers
+    float4 r4[NG];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) {
+      const int g = lane + 32 * k;
+      r4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (4 * g + 3 < n) {
+        r4[k] = __ldg(reinterpret_cast<const float4*>(r) + g);
+      } else if (g < ld4) {  // the ragged last granule: only the n entries of r are read
+        const int i = 4 * g;
+        r4[k].x = __ldg(r + i);
+        if (i + 1 < n) r4[k].y = __ldg(r + i + 1);
+        if (i + 2 < n) r4[k].z = __ldg(r + i + 2);
+      }
+    }
+    float mx = 0.f;
+    long long it = 0;
+    for (long long blk = blockIdx.x; blk < nblocks; blk += gridDim.x, ++it) {
+      const int s = (int)(it % kXStages);
+      if (!mbar_wait(&full[s], (unsigned)((it / kXStages) & 1), &s_err)) break;
+      const long long j0 = blk * cols_per_stage;
+      const int cols = (int)min((long long)cols_per_stage, (long long)p - j0);
+      const unsigned char* base = xsm + (size_t)s * cols_per_stage * col_bytes;
+      for (int cc = warp; cc < cols; cc += kConsumerWarps) {
+        const float4* col = reinterpret_cast<const float4*>(base + (size_t)cc * col_bytes);
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const int g = lane + 32 * k;
+          if (g < ld4) {
+            const float4 v = mask_tail(col[g], g, n);
+            acc = __fmaf_rn(v.x, r4[k].x, acc);
+            acc = __fmaf_rn(v.y, r4[k].y, acc);
+            acc = __fmaf_rn(v.z, r4[k].z, acc);
+            acc = __fmaf_rn(v.w, r4[k].w, acc);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = __fadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (lane == 0) c[j0 + cc] = acc;
+        mx = fmaxf(mx, fabsf(acc));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    // the maximum does not depend on the order in which warps report it
+    if (lane == 0 && cmax_bits) atomicMax(cmax_bits, __float_as_uint(mx));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_err != 0 && cmax_bits) atomicMax(cmax_bits, 0x7fc00000u);  // NaN: a wait timed out
+}
+
+template <int NG>
 lasso_status launch_xtr(const float* X, int64_t n, int64_t p, int64_t ldx, const float* r, float* c, unsigned* cmax,
                         cudaStream_t st) {
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xtr_f32_kernel<NG, U>, kXtrThreads, 0));
-  if (per_sm < 1) per_sm = 1;
-  const long long groups = (p + U - 1) / U;
-  const long long need = (groups + (kXtrThreads / 32) - 1) / (kXtrThreads / 32);
-  const int grid = (int)std::min<long long>((long long)sms * per_sm, need);
-  xtr_f32_kernel<NG, U><<<grid, kXtrThreads, 0, st>>>(X, ldx, (int)n, (int)p, r, c, cmax);
+  const int ld4 = (int)((n + 3) / 4);
+  const int col_bytes = 16 * ld4;
+  const int cols = std::max(1, kStageTarget / col_bytes);
+  const size_t smem = (size_t)kXStages * cols * col_bytes;
+  CUDA_TRY(cudaFuncSetAttribute(xtr_f32_kernel<NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long blocks = (p + cols - 1) / cols;
+  const int grid = (int)std::min<long long>(2ll * sms, blocks);
+  xtr_f32_kernel<NG><<<grid, kXtrThreads, smem, st>>>(X, ldx, (int)n, (int)p, cols, r, c, cmax);
   CUDA_TRY(cudaGetLastError());
   return LASSO_OK;
 }
@@ -136,11 +175,10 @@ extern "C" lasso_status lasso_correlations_f32(const float* X, int64_t n, int64_
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned* cm = reinterpret_cast<unsigned*>(cmax);
   if (cm) CUDA_TRY(cudaMemsetAsync(cm, 0, sizeof(unsigned), st));
-  // NG float4 granules per lane cover n <= 128 NG rows; U * NG = 16 keeps
-  // 8 KB of loads in flight per warp at every n
-  if (n <= 128) return launch_xtr<1, 16>(X, n, p, ldx, r, c, cm, st);
-  if (n <= 256) return launch_xtr<2, 8>(X, n, p, ldx, r, c, cm, st);
-  if (n <= 512) return launch_xtr<4, 4>(X, n, p, ldx, r, c, cm, st);
-  if (n <= 1024) return launch_xtr<8, 2>(X, n, p, ldx, r, c, cm, st);
-  return launch_xtr<16, 1>(X, n, p, ldx, r, c, cm, st);
+  // NG float4 granules per lane cover n <= 128 NG rows
+  if (n <= 128) return launch_xtr<1>(X, n, p, ldx, r, c, cm, st);
+  if (n <= 256) return launch_xtr<2>(X, n, p, ldx, r, c, cm, st);
+  if (n <= 512) return launch_xtr<4>(X, n, p, ldx, r, c, cm, st);
+  if (n <= 1024) return launch_xtr<8>(X, n, p, ldx, r, c, cm, st);
+  return launch_xtr<16>(X, n, p, ldx, r, c, cm, st);
 }

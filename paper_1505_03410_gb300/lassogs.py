@@ -31,7 +31,8 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 # every symbol include/lassogs.h declares
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
             "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch",
-            "lasso_correlations_bf16", "lasso_correlations_f32")
+            "lasso_correlations_bf16", "lasso_correlations_f32", "lasso_batch_tune_candidates",
+            "lasso_batch_tune_workspace_size", "lasso_batch_tune")
 
 
 class LassoError(RuntimeError):
@@ -44,7 +45,8 @@ class LassoOpts(ctypes.Structure):
     _fields_ = [("screen_period", ctypes.c_int32), ("dual_point", ctypes.c_int32),
                 ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
-                ("gemm_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("gemm_dtype", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
+                ("gemm_tile_n", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class LassoPathStats(ctypes.Structure):
@@ -96,6 +98,14 @@ def load(path: str | None = None):
             lib.lasso_correlations_bf16.restype = ctypes.c_int
             lib.lasso_correlations_f32.argtypes = [V, I64, I64, I64, V, V, V, V]
             lib.lasso_correlations_f32.restype = ctypes.c_int
+            lib.lasso_batch_tune_candidates.argtypes = []
+            lib.lasso_batch_tune_candidates.restype = I32
+            lib.lasso_batch_tune_workspace_size.argtypes = [I64, I64, I64, I32]
+            lib.lasso_batch_tune_workspace_size.restype = SZ
+            lib.lasso_batch_tune.argtypes = [V, I64, I64, I64, V, I64, V, I64, I64, V, I32, V, I64,
+                                             ctypes.POINTER(LassoOpts), I32, I32, ctypes.POINTER(LassoOpts), V, V, SZ,
+                                             V]
+            lib.lasso_batch_tune.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
             lib.lasso_last_error.restype = ctypes.c_char_p
             _lib = lib
@@ -222,6 +232,58 @@ def lasso_correlations_f32(X, n, p, ldx, r, c, cmax, stream) -> int:
         return None if x is None or x == 0 else ctypes.c_void_p(int(x))
     return _check(load().lasso_correlations_f32(vp(X), int(n), int(p), int(ldx), vp(r), vp(c), vp(cmax),
                                                 vp(stream)))
+
+
+def lasso_batch_tune_candidates() -> int:
+    return int(load().lasso_batch_tune_candidates())
+
+
+def lasso_batch_tune_workspace_size(n, p, sample, lambdas) -> int:
+    return int(load().lasso_batch_tune_workspace_size(int(n), int(p), int(sample), int(lambdas)))
+
+
+def lasso_batch_tune(X, n, p, ldx, Y, ldy, row_mask, ldm, B, lambda_ratios, T, beta0, ldb0, opts, sample, lambdas,
+                     tuned, times_ms, workspace, workspace_bytes, stream) -> int:
+    """Direct call of the launch-shape autotuner (pointers as integers; tuned
+    a LassoOpts to fill; times_ms a float32 numpy array or None)."""
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    return _check(load().lasso_batch_tune(vp(X), int(n), int(p), int(ldx), vp(Y), int(ldy), vp(row_mask), int(ldm),
+                                          int(B), vp(lambda_ratios), int(T), vp(beta0), int(ldb0),
+                                          ctypes.byref(opts) if opts is not None else None, int(sample),
+                                          int(lambdas), ctypes.byref(tuned),
+                                          times_ms.ctypes.data_as(ctypes.c_void_p) if times_ms is not None else None,
+                                          vp(workspace), int(workspace_bytes), vp(stream)))
+
+
+def tune_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, sample=None, lambdas=None, stream=None):
+    """Run lasso_batch_tune on torch CUDA tensors (the layouts of solve_batch).
+    Returns (tuned LassoOpts, per-candidate times in ms as a numpy array)."""
+    import torch
+    p, ldx = XT.shape
+    B, ldy = Y.shape
+    n = int(n if n is not None else ldy)
+    T = int(ratios.shape[0])
+    opts = opts or lasso_default_opts()
+    sample = int(sample if sample is not None else min(B, 2 * torch.cuda.get_device_properties(XT.device)
+                                                       .multi_processor_count))
+    lambdas = int(lambdas if lambdas is not None else min(T, 5))
+    need = lasso_batch_tune_workspace_size(n, p, sample, lambdas)
+    ws = torch.empty(need, dtype=torch.uint8, device=XT.device)
+    times = np.zeros(lasso_batch_tune_candidates(), dtype=np.float32)
+    tuned = LassoOpts()
+    s = stream if stream is not None else torch.cuda.current_stream(XT.device)
+
+    def vp(x):
+        return None if x is None or x == 0 else ctypes.c_void_p(int(x))
+    _check(load().lasso_batch_tune(vp(XT.data_ptr()), n, p, ldx, vp(Y.data_ptr()), ldy,
+                                   vp(row_mask.data_ptr() if row_mask is not None else None),
+                                   row_mask.shape[1] if row_mask is not None else 0, B, vp(ratios.data_ptr()), T,
+                                   vp(beta0.data_ptr() if beta0 is not None else None),
+                                   beta0.shape[1] if beta0 is not None else 0, ctypes.byref(opts), sample, lambdas,
+                                   ctypes.byref(tuned), times.ctypes.data_as(ctypes.c_void_p), vp(ws.data_ptr()),
+                                   need, vp(s.cuda_stream)))
+    return tuned, times
 
 
 def stats_to_numpy(stats_tensor) -> np.ndarray:

@@ -199,3 +199,54 @@ def test_batch_captured_in_cuda_graph(pkg):
         results.append(gr)
     o = oracle.lasso_batch(prob["XT"], Y * rmask * 1.5, ratios, row_mask=rmask, n=160, gap_tol_rel=1e-9)
     check_batch(results[1], o)
+
+
+def test_autotuner_picks_a_shape_and_keeps_results(pkg):
+    """lasso_batch_tune times its six launch shapes and returns the fastest;
+    solving with the tuned options gives bit-identical coefficients, masks
+    and pass counts to the default shape (every shape makes the FP64 test's
+    decisions), and both match the oracle."""
+    prob, Y, rmask = _subsample_problem(209, 200, 2000, 40, correlated=False)
+    ratios = oracle.lambda_ratios(8, 1.5)
+    dev = torch.device("cuda:0")
+    Xd = torch.from_numpy(np.ascontiguousarray(prob["XT"], dtype=np.float32)).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    Md = torch.from_numpy(rmask).to(dev)
+    r = torch.from_numpy(ratios).to(dev)
+    base = pkg.lasso_default_opts(gap_tol_rel=1e-9)
+    tuned, times = pkg.tune_batch(Xd, Yd, r, n=200, row_mask=Md, opts=base, sample=16, lambdas=4)
+    assert np.all(times > 0)
+    k = int(np.argmin(times))
+    shapes = [(pkg.LASSO_F32, 2, 0), (pkg.LASSO_F32, 1, 0), (pkg.LASSO_BF16, 2, 128), (pkg.LASSO_BF16, 1, 128),
+              (pkg.LASSO_BF16, 2, 256), (pkg.LASSO_BF16, 1, 256)]
+    assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n) == shapes[k]
+    assert tuned.gap_tol_rel == 1e-9
+    outs = {}
+    for name, o in (("default", base), ("tuned", tuned)):
+        out = pkg.solve_batch(Xd, Yd, r, n=200, row_mask=Md, opts=o)
+        torch.cuda.synchronize()
+        st = pkg.stats_to_numpy(out["stats"]).reshape(40, len(ratios))
+        outs[name] = (out["beta"].cpu().numpy(), out["mask"].cpu().numpy(), st)
+    np.testing.assert_array_equal(outs["default"][0], outs["tuned"][0])
+    np.testing.assert_array_equal(outs["default"][1], outs["tuned"][1])
+    np.testing.assert_array_equal(outs["default"][2]["epochs"], outs["tuned"][2]["epochs"])
+    pick = [0, 17, 39]
+    o = oracle.lasso_batch(prob["XT"], (Y * rmask)[pick], ratios, row_mask=rmask[pick], n=200, gap_tol_rel=1e-9)
+    g = dict(beta=outs["tuned"][0][pick], mask=outs["tuned"][1][pick].view(np.uint32), stats=outs["tuned"][2][pick])
+    check_batch(g, o)
+
+
+@pytest.mark.parametrize("per_sm,tile", [(1, 64), (1, 256), (2, 64)])
+def test_batch_launch_shapes(pkg, per_sm, tile):
+    """One CTA per SM (no register cap) and every tensor-core N tile give the
+    oracle's results."""
+    prob, Y, rmask = _subsample_problem(210, 333, 1500, 9, correlated=True)
+    ratios = oracle.lambda_ratios(10, 2.0)
+    opt = dict(gap_tol_rel=1e-9, xtr_scope=1)
+    g = run_gpu_batch(pkg, prob["XT"], 333, Y, rmask, ratios, gemm_dtype=pkg.LASSO_BF16, batch_ctas_per_sm=per_sm,
+                      gemm_tile_n=tile, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=333, **opt)
+    check_batch(g, o)
+    g1 = run_gpu_batch(pkg, prob["XT"], 333, Y, rmask, ratios, gemm_dtype=pkg.LASSO_F32, batch_ctas_per_sm=per_sm,
+                       **opt)
+    check_batch(g1, o)
