@@ -90,6 +90,50 @@ __device__ __forceinline__ float warp_dot_f32(const float* col, const float4 (&r
   return warp_sum_f(__fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3)));
 }
 
+// Two columns at once against the same rho: both columns' loads are issued
+// before either is reduced (twice the bytes in flight per warp).  Each result
+// is computed exactly as warp_dot_f32 computes it.
+template <int NG>
+__device__ __forceinline__ void warp_dot_f32_2(const float* ca, const float* cb, const float4 (&r)[NG], int ld4, int n,
+                                               float& outa, float& outb) {
+  int lane = threadIdx.x & 31;
+  float4 xa[NG], xb[NG];
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    int g = lane + 32 * k;
+    xa[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    xb[k] = xa[k];
+    if (g < ld4) {
+      xa[k] = ld_x4(ca, g, n);
+      xb[k] = ld_x4(cb, g, n);
+    }
+  }
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll
+  for (int k = 0; k < NG; ++k) {
+    int g = lane + 32 * k;
+    if (g < ld4) {
+      a0 = __fmaf_rn(xa[k].x, r[k].x, a0);
+      a1 = __fmaf_rn(xa[k].y, r[k].y, a1);
+      a2 = __fmaf_rn(xa[k].z, r[k].z, a2);
+      a3 = __fmaf_rn(xa[k].w, r[k].w, a3);
+      b0 = __fmaf_rn(xb[k].x, r[k].x, b0);
+      b1 = __fmaf_rn(xb[k].y, r[k].y, b1);
+      b2 = __fmaf_rn(xb[k].z, r[k].z, b2);
+      b3 = __fmaf_rn(xb[k].w, r[k].w, b3);
+    }
+  }
+  float sa = __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, a3));
+  float sb = __fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, b3));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa = __fadd_rn(sa, __shfl_xor_sync(0xffffffffu, sa, o));
+    sb = __fadd_rn(sb, __shfl_xor_sync(0xffffffffu, sb, o));
+  }
+  outa = sa;
+  outb = sb;
+}
+
 // Exact (double-float, order-independent) dot of column j with rho given as
 // two planes in global memory; bound >= sum_i |x_ij rho_i|.  Whole warp.
 template <int NG, bool XLO, typename Ctx>

@@ -832,6 +832,29 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                     need = !(__fsub_ru(mend, __ldcg(mrp + il)) < sk);
                   }
                   unsigned needm = __ballot_sync(0xffffffffu, need);
+                  // the verdict for position i from its FP32 correlation c with the
+                  // snapshot sh: stays zero (certificate renewed) or enters
+                  auto decide = [&](int i, int j, float c, const float* sh) -> bool {
+                    const float nf = __ldcg(WS(float, nrmf) + j);
+                    const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
+                    bool enters;
+                    if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
+                    else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
+                    else {
+                      const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
+                      df2 nb, d;
+                      cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
+                      enters = !df_is_zero(d);
+                    }
+                    if (enters) {
+                      if (lane == 0) atomicMin(&ctl->fstar, i);
+                    } else if (lane == 0) {
+                      const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
+                      WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
+                      mrp[i] = __ldcg(WS(float, msnap) + seg);
+                    }
+                    return enters;
+                  };
                   while (needm) {
                     const int i = base + __ffs(needm) - 1;
                     needm &= needm - 1;
@@ -853,27 +876,32 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                       loaded = seg;
                     }
                     const int j = __ldcg(WS(int, A) + i);
-                    const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-                    const float nf = __ldcg(WS(float, nrmf) + j);
-                    const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
-                    bool enters;
-                    if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
-                    else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
-                    else {
-                      const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
-                      df2 nb, d;
-                      cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
-                      enters = !df_is_zero(d);
-                    }
-                    if (enters) {
-                      if (lane == 0) atomicMin(&ctl->fstar, i);
-                      stop_warp = true;
-                      break;
-                    }
-                    if (lane == 0) {
-                      const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
-                      WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
-                      mrp[i] = __ldcg(WS(float, msnap) + seg);
+                    // the next needed position shares the snapshot when no chain
+                    // entry lies between them: verify both with one pass of loads
+                    // (up to 8 granules per lane; longer columns keep one)
+                    constexpr bool kPair = NG <= 8;
+                    const int seg_end = seg < nc ? __ldcg(WS(int, chain) + seg) : 0x7fffffff;
+                    const int i2 = needm ? base + __ffs(needm) - 1 : 0x7fffffff;
+                    if (kPair && i2 < seg_end) {
+                      const int j2 = __ldcg(WS(int, A) + i2);
+                      float c, c2;
+                      warp_dot_f32_2<NG>(a.Xh + (long long)j * a.ldx, a.Xh + (long long)j2 * a.ldx, r4, a.ld4, a.n,
+                                         c, c2);
+                      if (decide(i, j, c, sh)) {
+                        stop_warp = true;
+                        break;
+                      }
+                      needm &= needm - 1;
+                      if (decide(i2, j2, c2, sh)) {
+                        stop_warp = true;
+                        break;
+                      }
+                    } else {
+                      const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
+                      if (decide(i, j, c, sh)) {
+                        stop_warp = true;
+                        break;
+                      }
                     }
                   }
                 }

@@ -258,7 +258,9 @@ def lasso_batch_tune(X, n, p, ldx, Y, ldy, row_mask, ldm, B, lambda_ratios, T, b
 
 def tune_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, sample=None, lambdas=None, stream=None):
     """Run lasso_batch_tune on torch CUDA tensors (the layouts of solve_batch).
-    Returns (tuned LassoOpts, per-candidate times in ms as a numpy array)."""
+    Defaults: one resident wave of problems (2 x SMs) over the first quarter of
+    the grid (at least 5 lambdas).  Returns (tuned LassoOpts, per-candidate
+    times in ms as a numpy array)."""
     import torch
     p, ldx = XT.shape
     B, ldy = Y.shape
@@ -267,7 +269,9 @@ def tune_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, samp
     opts = opts or lasso_default_opts()
     sample = int(sample if sample is not None else min(B, 2 * torch.cuda.get_device_properties(XT.device)
                                                        .multi_processor_count))
-    lambdas = int(lambdas if lambdas is not None else min(T, 5))
+    # the first lambdas are check-dominated (where the tensor-core product
+    # helps most); a quarter of the grid weighs the passes of the later ones
+    lambdas = int(lambdas if lambdas is not None else min(T, max(5, T // 4)))
     need = lasso_batch_tune_workspace_size(n, p, sample, lambdas)
     ws = torch.empty(need, dtype=torch.uint8, device=XT.device)
     times = np.zeros(lasso_batch_tune_candidates(), dtype=np.float32)
