@@ -308,14 +308,25 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
       // |partial sums| <= ||x_j|| ||rho|| <= nf * rho_bound
       float sc, isc;
       limb_scale(2.0f * r0.nf * rho_bound + 1e-30f, sc, isc);
-      limbs3 L = limbs_add(limbs_add(to_limbs(S0, sc), to_limbs(C0, sc)),
-                           limbs_add(to_limbs(S1, sc), to_limbs(C1, sc)));
-      if (kFour)
-        L = limbs_add(L, limbs_add(limbs_add(to_limbs(S2, sc), to_limbs(C2, sc)),
-                                   limbs_add(to_limbs(S3, sc), to_limbs(C3, sc))));
-      // carries out of the two low limbs before the cross-thread sum: every
-      // limb is then below 2^22 + 1 in magnitude, and 128 of them fit int32
-      L = limbs_norm(L);
+      limbs3 L;
+      if (kFour) {
+        L = limbs_add(limbs_add(limbs_add(to_limbs(S0, sc), to_limbs(C0, sc)),
+                                limbs_add(to_limbs(S1, sc), to_limbs(C1, sc))),
+                      limbs_add(limbs_add(to_limbs(S2, sc), to_limbs(C2, sc)),
+                                limbs_add(to_limbs(S3, sc), to_limbs(C3, sc))));
+        // carries out of the two low limbs before the cross-thread sum: every
+        // limb is then below 2^22 + 1 in magnitude, and 128 of them fit int32
+        L = limbs_norm(L);
+      } else {
+        // one granule per lane: fold the two compensated sums first (an
+        // error-free TwoSum of the leading parts, the tails added in FP32,
+        // far below the double-float's 2^-48), then two limb conversions;
+        // two partials per thread keep every limb sum inside int32 unnormalised
+        float sh, se;
+        two_sum(S0, S1, sh, se);
+        const float st = __fadd_rn(__fadd_rn(C0, C1), se);
+        L = limbs_add(to_limbs(sh, sc), to_limbs(st, sc));
+      }
       L = warp_limbs_sum(L);
       limbs3 Tl = L;
       if (CW > 1) {
