@@ -71,6 +71,21 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_ranks(total_ms, solves, device=None):
+    """Whole-job figures over the ranks of an initialised process group: the
+    timed region is the slowest rank's (max), the certified solves add up.
+    Without a group (one process) the inputs come back unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), int(solves)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(solves)], dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return float(t.item()), int(round(float(s.item())))
+
+
 def _workload():
     import gen
     return gen.workload2()
@@ -275,15 +290,7 @@ def run_ours(args):
     xcols = int(st["x_columns"].sum())
     total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        s = torch.tensor([solves], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        solves_all = int(s.item())
-    else:
-        solves_all = solves
+    total_ms, solves_all = aggregate_ranks(total_ms, solves, dev)
     value = solves_all / (total_ms / 1e3)
 
     # e2e: inputs from pinned host memory, results back to the host, inside the step
@@ -317,13 +324,7 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1)
     h2d = XT_h.numel() * XT_h.element_size() + y_h.numel() * 8 + r_h.numel() * 8
     d2h = beta_h.numel() * 8 + stats_h.numel()
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-        s = torch.tensor([e2e_solves], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        e2e_solves = int(s.item())
+    e2e_ms, e2e_solves = aggregate_ranks(e2e_ms, e2e_solves, dev)
     e2e_value = e2e_solves / (e2e_ms / 1e3)
 
     peaks = _peaks()

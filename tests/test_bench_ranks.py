@@ -1,0 +1,56 @@
+"""The bench's multi-process path on the CPU: two gloo ranks (127.0.0.1)
+aggregate their timed regions the way `bench.py --gpus N` does under
+torchrun -- the slowest rank's time, the sum of the certified solves -- and
+the reference arm does its work on rank 0 only."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, solves = bench.aggregate_ranks(100.0 + 50.0 * rank, 10 + rank)
+        q.put((rank, ms, solves))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29611
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    # every rank sees the whole job: max time 150 ms, 10 + 11 solves
+    assert res == [(0, 150.0, 21), (1, 150.0, 21)]
+
+
+def test_single_process_aggregate_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate_ranks(12.5, 7) == (12.5, 7)
+
+
+def test_reference_arm_does_nothing_off_rank_zero():
+    """Under torchrun only rank 0 runs and prints the reference line."""
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
