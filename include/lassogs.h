@@ -69,8 +69,12 @@ typedef struct lasso_opts {
   int32_t batch_ctas_per_sm; /* batched solver: resident CTAs per SM, 1 or 2 (0 = 2, the default).
                                 With 1 the kernel may use up to 255 registers per thread */
   int32_t gemm_tile_n;   /* lockstep batches: N tile of the tensor-core product, 64, 128 or 256
-                            (0 = 128).  lasso_batch_tune picks these two and gemm_dtype */
-  int32_t reserved;      /* must be zero */
+                            (0 = 128) */
+  int32_t batch_group;   /* batched solver with gemm_dtype = LASSO_F32: CTAs per problem, 1..64
+                            (0 = 1).  A group splits the features of its problem into slices as
+                            the single path does; for designs that do not fit L2 it spreads each
+                            problem's column reads over several SMs.  lasso_batch_tune picks this,
+                            batch_ctas_per_sm, gemm_tile_n and gemm_dtype */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */
@@ -182,11 +186,12 @@ lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, 
 
 /* Launch-shape autotuner for lasso_batch.  Times every candidate shape
  * (lasso_batch_tune_candidates() of them: per-CTA FP32 checks or lockstep
- * split-BF16 products, 1 or 2 solver CTAs per SM, and for lockstep an N tile
- * of 128 or 256) on the first `sample` problems over the first `lambdas`
+ * split-BF16 products, 1 or 2 solver CTAs per SM, for lockstep an N tile of
+ * 128 or 256, for FP32 checks groups of 8 or 32 CTAs per problem) on the
+ * first `sample` problems over the first `lambdas`
  * ratios of the grid -- a warm-up run, then a run timed with CUDA events on
  * `stream` -- and writes *opts with the fastest gemm_dtype,
- * batch_ctas_per_sm and gemm_tile_n to *tuned.  Every candidate makes the
+ * batch_ctas_per_sm, gemm_tile_n and batch_group to *tuned.  Every candidate makes the
  * same screening decisions (each equal to the FP64 test's), so the choice
  * changes the time, not the results.  Arguments as for lasso_batch;
  * 1 <= sample <= B, 1 <= lambdas <= T; times_ms (host, one float per

@@ -40,7 +40,10 @@ lasso_status check_opts(const lasso_opts& o) {
     return set_error(LASSO_ERR_INVALID_ARG, "batch_ctas_per_sm must be 0, 1 or 2");
   if (o.gemm_tile_n != 0 && o.gemm_tile_n != 64 && o.gemm_tile_n != 128 && o.gemm_tile_n != 256)
     return set_error(LASSO_ERR_INVALID_ARG, "gemm_tile_n must be 0, 64, 128 or 256");
-  if (o.reserved != 0) return set_error(LASSO_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.batch_group < 0 || o.batch_group > 64)
+    return set_error(LASSO_ERR_INVALID_ARG, "batch_group must lie in [0, 64]");
+  if (o.batch_group > 1 && o.gemm_dtype != LASSO_F32)
+    return set_error(LASSO_ERR_INVALID_ARG, "batch_group > 1 needs gemm_dtype = LASSO_F32");
   return LASSO_OK;
 }
 

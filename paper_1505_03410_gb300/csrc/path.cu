@@ -59,6 +59,7 @@ struct Ctrl {
   // end of pass, setup of a round) and event counts (rounds, rollbacks)
   unsigned long long prof[8];
   int win;                    // positions a round may span (adaptive, see the passes)
+  int prob;                   // groups of CTAs: the problem CTA 0 took from the queue
 };
 
 struct Args {
@@ -92,6 +93,7 @@ struct Args {
   const double* beta0;  // starting points beta0[j + b * ldb0], or null
   long long ldb0;
   int* queue;       // next problem to take
+  int gsize;        // CTAs per problem (a group shares one workspace region and its barrier)
   double tol;       // gap_tol_rel
   // lockstep batches: one launch per lambda range [t0, t1), workspace region
   // per problem (not per CTA), and the first check of each lambda reads
@@ -146,13 +148,17 @@ __device__ __forceinline__ uint32_t chain_row_bits(const Args& a, int b) {
 constexpr int kBatchRowsPerThread = 8;
 static_assert(kBatchRowsPerThread * kThreads >= kMaxRows, "a thread's rows must cover n <= kMaxRows");
 
-// Per-problem set-up of a batched CTA (the single path does this with the
+// Per-problem set-up of a batched problem (the single path does this with the
 // precompute kernels): y restricted to the problem's rows, rho = y - X beta0,
-// ||y||^2,
-// and for every column the norm over those rows and x_j^T y, whose largest
-// magnitude is lambda_max (Sec. 1.2).  FP64 accumulation.
+// ||y||^2, and for every column the norm over those rows and x_j^T y, whose
+// largest magnitude is lambda_max (Sec. 1.2).  FP64 accumulation.  The parts:
+// reset (the control fields a problem starts from), rows (y, rho, ||y||^2),
+// the columns [j0, j1) and final (lambda_max and the input checks).  One CTA
+// per problem runs them all; in a group of CTAs every CTA runs the columns of
+// its slice, CTA 0 the rest, with group barriers in between.
 template <bool XLO>
-__device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* dbuf) {
+__device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* dbuf, int j0, int j1, bool reset,
+                            bool rows, bool final) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = kThreads / 32;
   double* yb = reinterpret_cast<double*>(wsb + a.o_yb);
   float* rh = reinterpret_cast<float*>(wsb + a.o_rho_h);
@@ -164,17 +170,19 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
   float4* ftab = reinterpret_cast<float4*>(wsb + a.o_ftab);
   float2* bdf = reinterpret_cast<float2*>(wsb + a.o_bdf);
   float2* b0df = reinterpret_cast<float2*>(wsb + a.o_b0df);
-  if (tid == 0) {
-    ctl->err = 0;
-    ctl->nonfinite = 0;
-    ctl->m_bits = 0ull;
-    ctl->mlo_bits = 0u;
-    ctl->nzl = 0;
+  if (reset) {
+    if (tid == 0) {
+      ctl->err = 0;
+      ctl->nonfinite = 0;
+      ctl->m_bits = 0ull;
+      ctl->mlo_bits = 0u;
+      ctl->nzl = 0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   double yy = 0.0;
   bool finite = true;
-  for (int i = tid; i < a.ldw; i += kThreads) {
+  for (int i = tid; rows && i < a.ldw; i += kThreads) {
     const bool in = i < a.n && (a.rmask == nullptr || a.rmask[i + (size_t)b * a.ldm] != 0);
     const double v = in ? a.y[i + (size_t)b * a.ldy] : 0.0;
     finite = finite && isfinite(v);
@@ -186,8 +194,11 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
     r0h[i] = d.h;
     r0l[i] = d.l;
   }
-  yy = block_sum_d(yy, dbuf);
-  for (int j = warp; j < a.p; j += nwarps) {
+  if (rows) {
+    yy = block_sum_d(yy, dbuf);
+    if (tid == 0) ctl->yy = yy;
+  }
+  for (int j = j0 + warp; j < j1; j += nwarps) {
     const float* col = a.Xh + (long long)j * a.ldx;
     const float* coll = XLO ? a.Xl + (long long)j * a.ldx : nullptr;
     double s2 = 0.0, sy = 0.0;
@@ -198,7 +209,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
       if (XLO && in) x = __dadd_rn(x, (double)__ldg(coll + i));
       fin = fin && isfinite(x);
       s2 = __fma_rn(x, x, s2);
-      sy = __fma_rn(x, yb[i], sy);
+      sy = __fma_rn(x, in ? a.y[i + (size_t)b * a.ldy] : 0.0, sy);
     }
     s2 = warp_sum_d(s2);
     sy = warp_sum_d(sy);
@@ -216,7 +227,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
       b0df[j] = make_float2(bd.h, bd.l);
     }
   }
-  if (a.beta0 != nullptr) {
+  if (rows && a.beta0 != nullptr) {
     // rho = y - X beta0 on the problem's rows: the nonzero terms are
     // subtracted in ascending j, each product and difference rounded once
     __shared__ int s_j[kThreads];
@@ -273,23 +284,26 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
   }
   if (!finite) atomicExch(&ctl->nonfinite, 1);
   __syncthreads();
-  if (tid == 0) {
-    ctl->lambda_max = __longlong_as_double((long long)ctl->m_bits);
-    ctl->m_bits = 0ull;
-    ctl->yy = yy;
-    ctl->eps = a.tol * yy;
-    bool bad = !(ctl->lambda_max > 0.0);
-    for (int t = 0; t < a.T; ++t) bad = bad || !(a.ratios[t] > 0.0 && a.ratios[t] <= 1.0);
-    if (ctl->nonfinite) ctl->err = kErrNonfinite;
-    else if (bad) ctl->err = kErrInvalidArg;
+  if (final) {
+    if (tid == 0) {
+      ctl->lambda_max = __longlong_as_double((long long)ctl->m_bits);
+      ctl->m_bits = 0ull;
+      ctl->eps = a.tol * ctl->yy;
+      bool bad = !(ctl->lambda_max > 0.0);
+      for (int t = 0; t < a.T; ++t) bad = bad || !(a.ratios[t] > 0.0 && a.ratios[t] <= 1.0);
+      if (ctl->nonfinite) ctl->err = kErrNonfinite;
+      else if (bad) ctl->err = kErrInvalidArg;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------- the kernel
 // BATCH = false: the whole grid cooperates on one problem (grid barriers).
-// BATCH = true: every CTA is a one-CTA "grid" with its own workspace copy and
-// solves problems taken from a queue, one whole path at a time.
+// BATCH = true: groups of a.gsize CTAs (one CTA by default) each have their
+// own workspace region, whose control block carries the group's barrier, and
+// solve problems taken from a queue, one whole path at a time; within a group
+// the CTAs split the features into slices as the single path does.
 // MINB: CTAs per SM the launch bounds promise (registers per thread <= 65536 / (256 MINB))
 template <int NGC, int CW, bool XLO, bool BATCH, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
@@ -302,12 +316,14 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   __shared__ float fbuf[32];
   __shared__ int s_prob;
 
-  char* wsb = a.ws + (BATCH ? (size_t)blockIdx.x * a.cta_bytes : (size_t)0);
+  // G CTAs cooperate on one problem: the whole grid, or a group of the batch
+  const int G = BATCH ? a.gsize : (int)gridDim.x;
+  const int cta = (int)blockIdx.x % G, grp = (int)blockIdx.x / G;
+  char* wsb = a.ws + (BATCH ? (size_t)grp * a.cta_bytes : (size_t)0);
 #define WS(T, name) reinterpret_cast<T*>(wsb + a.o_##name)
   Ctrl* ctl = WS(Ctrl, ctrl);
-  const int cta = BATCH ? 0 : (int)blockIdx.x, G = BATCH ? 1 : (int)gridDim.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = kThreads / 32;
-  const int f0 = BATCH ? 0 : slice_begin(a, cta), f1 = BATCH ? a.p : slice_begin(a, cta + 1);
+  const int f0 = slice_begin(a, cta), f1 = slice_begin(a, cta + 1);
   // mask words of the slice: f0 is a multiple of 32 when the slice is not
   // empty; CTAs past the last feature (f0 == f1 == p) own no word
   const int wd0 = f0 >> 5, wd1 = f1 > f0 ? (f1 + 31) >> 5 : wd0;
@@ -328,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   long long tprof = clock64();
   // phase counters: thread 0 of CTA 0 (single path) or of every CTA (batched,
   // the counters of the problem it solved last)
-  const bool prof_thread = BATCH ? tid == 0 : (blockIdx.x == 0 && tid == 0);
+  const bool prof_thread = cta == 0 && tid == 0;
 #define PROF(k)                                   \
   do {                                            \
     if (prof_thread) {                            \
@@ -346,10 +362,25 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   for (int it = 0;; ++it) {
     int b = 0;
     if (BATCH) {
-      if (tid == 0) s_prob = atomicAdd(a.queue, 1);
-      __syncthreads();
-      b = s_prob;
-      __syncthreads();
+      if (G == 1) {
+        if (tid == 0) s_prob = atomicAdd(a.queue, 1);
+        __syncthreads();
+        b = s_prob;
+        __syncthreads();
+      } else {
+        // CTA 0 of the group takes the problem and resets the fields the
+        // set-up accumulates into; the group barrier publishes both
+        if (cta == 0 && tid == 0) {
+          ctl->err = 0;
+          ctl->nonfinite = 0;
+          ctl->m_bits = 0ull;
+          ctl->mlo_bits = 0u;
+          ctl->nzl = 0;
+          ctl->prob = atomicAdd(a.queue, 1);
+        }
+        if (!grid_sync(bc, bg, err, (unsigned)G)) break;
+        b = vload(ctl->prob);
+      }
       if (b >= a.B) break;
       if (a.lockstep) {
         // this problem's own region carries its state from launch to launch
@@ -362,14 +393,20 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                       a.ld4,         WS(int, A),     WS(int, chain),  WS(float4, ftab), WS(float2, bdf),
                       WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap), WS(float, msnap)};
         if (a.t0 == 0) {
-          batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+          batch_setup<XLO>(a, ctl, wsb, b, dbuf, 0, a.p, true, true, true);
           if (tid == 0) ctl->failed = 0;
           __syncthreads();
         } else if (vload(ctl->failed) != 0) {
           continue;  // its records were stamped when it failed
         }
+      } else if (G == 1) {
+        batch_setup<XLO>(a, ctl, wsb, b, dbuf, 0, a.p, true, true, true);
       } else {
-        batch_setup<XLO>(a, ctl, wsb, b, dbuf);
+        // every CTA: the columns of its slice; CTA 0: y, rho and ||y||^2, then lambda_max
+        batch_setup<XLO>(a, ctl, wsb, b, dbuf, f0, f1, false, cta == 0, false);
+        if (!grid_sync(bc, bg, err, (unsigned)G)) goto fail;
+        if (cta == 0) batch_setup<XLO>(a, ctl, wsb, b, dbuf, 0, 0, false, false, true);
+        if (!grid_sync(bc, bg, err, (unsigned)G)) goto fail;
       }
       if (prof_thread && (!a.lockstep || a.t0 == 0)) {
         for (int k = 0; k < 8; ++k) ctl->prof[k] = 0ull;
@@ -1021,22 +1058,30 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
     if (!BATCH) break;
     {
       const int e = vload(*err);
-      lasso_path_stats* so = a.stats + (size_t)b * a.T;
-      const int tf0 = a.lockstep ? a.t0 : 0;
-      for (int t = tf0 + tid; t < a.T; t += kThreads) {
-        lasso_path_stats st{};
-        st.lambda = vload(ctl->lambda_max) * a.ratios[t];
-        st.status = e;
-        so[t] = st;
+      // a group: every CTA has read the code before CTA 0 clears it (this
+      // barrier completes although it reports the pending error)
+      if (G > 1) grid_sync(bc, bg, err, (unsigned)G);
+      if (cta == 0) {
+        lasso_path_stats* so = a.stats + (size_t)b * a.T;
+        const int tf0 = a.lockstep ? a.t0 : 0;
+        for (int t = tf0 + tid; t < a.T; t += kThreads) {
+          lasso_path_stats st{};
+          st.lambda = vload(ctl->lambda_max) * a.ratios[t];
+          st.status = e;
+          so[t] = st;
+        }
+        for (size_t k = (size_t)tf0 * a.p + tid; k < (size_t)a.T * a.p; k += kThreads)
+          a.beta_out[(size_t)b * a.T * a.p + k] = 0.0;
+        __syncthreads();
+        if (tid == 0) {
+          ctl->err = 0;
+          ctl->failed = e;
+        }
+        __syncthreads();
       }
-      for (size_t k = (size_t)tf0 * a.p + tid; k < (size_t)a.T * a.p; k += kThreads)
-        a.beta_out[(size_t)b * a.T * a.p + k] = 0.0;
-      __syncthreads();
-      if (tid == 0) {
-        ctl->err = 0;
-        ctl->failed = e;
-      }
-      __syncthreads();
+      // after a timed-out wait the group's barrier may be out of step: the
+      // group stops, and the other groups take the remaining problems
+      if (G > 1 && e == kErrTimeout) break;
     }
   }
 #undef GSYNC
@@ -1563,6 +1608,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   a.Xl = nullptr;
   a.ldx = ldx;
   a.fs = (int)((p + 31) / 32 * 32);
+  a.gsize = 1;
   const ChainShape cs = chain_shape(n, true);
   const int per_sm = o.batch_ctas_per_sm == 1 ? 1 : 2;
   const int grid = batch_grid(B, d.sms, per_sm);  // <= the regions the layout holds
@@ -1571,6 +1617,26 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
   CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  if (!lockstep && o.batch_group > 1) {
+    // groups of CTAs per problem: every group's CTAs must be resident together
+    // (their barrier), so the launch is cooperative and fills the resident CTAs
+    const int gs = o.batch_group;
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, dyn));
+    const int resident = d.sms * std::min(occ, per_sm);
+    const int groups = (int)std::min<int64_t>(B, resident / gs);
+    if (groups < 1)
+      return set_error(LASSO_ERR_INVALID_ARG, "batch_group %d exceeds the %d resident CTAs", gs, resident);
+    a.gsize = gs;
+    const long long fsz = (p + gs - 1) / gs;
+    a.fs = (int)((fsz + 31) / 32 * 32);
+    // each group's control block (its barrier count) starts at zero
+    CUDA_TRY(cudaMemset2DAsync(a.ws + a.o_ctrl, a.cta_bytes, 0, sizeof(Ctrl), (size_t)groups, stream));
+    CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
+    void* params[] = {&a};
+    CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(groups * gs), dim3(kThreads), params, dyn, stream));
+    return LASSO_OK;
+  }
   if (!lockstep) {
     // each CTA solves whole paths; its first checks are CUDA-core FP32 passes
     CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));

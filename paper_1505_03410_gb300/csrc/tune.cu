@@ -3,12 +3,14 @@
 // The candidates differ only in how the work is laid out on the GPU: where
 // the first check of each lambda gets X^T rho (per-CTA FP32 passes or one
 // split-BF16 tensor-core product per lambda), how many solver CTAs share an
-// SM (two, at 128 registers per thread, or one), and the N tile of the
-// tensor-core product.  Every candidate makes the same screening decisions
-// (each equals the FP64 test's), so the choice changes the time, never the
-// result.  Each candidate solves the same sample of problems over the first
-// lambdas of the grid twice (a warm-up, then a run timed with CUDA events on
-// the caller's stream), and the fastest is returned.
+// SM (two, at 128 registers per thread, or one), the N tile of the
+// tensor-core product, and how many CTAs work on one problem (1, 8 or 32).
+// Every candidate makes the same screening decisions (each equals the FP64
+// test's), so the choice changes the time, never the result.  Each candidate
+// solves the same sample of problems over the first lambdas of the grid
+// twice (a warm-up, then a run timed with CUDA events on the caller's
+// stream), and the fastest is returned.  A group too large for the resident
+// CTAs of this GPU is skipped (its time is reported as -1).
 #include <algorithm>
 #include <cstring>
 
@@ -20,12 +22,12 @@ namespace lassogs {
 namespace {
 
 struct Candidate {
-  int32_t dtype, per_sm, tile_n;
+  int32_t dtype, per_sm, tile_n, group;
 };
 
 constexpr Candidate kCandidates[] = {
-    {LASSO_F32, 2, 0},    {LASSO_F32, 1, 0},    {LASSO_BF16, 2, 128},
-    {LASSO_BF16, 1, 128}, {LASSO_BF16, 2, 256}, {LASSO_BF16, 1, 256},
+    {LASSO_F32, 2, 0, 1},    {LASSO_F32, 1, 0, 1},    {LASSO_BF16, 2, 128, 1}, {LASSO_BF16, 1, 128, 1},
+    {LASSO_BF16, 2, 256, 1}, {LASSO_BF16, 1, 256, 1}, {LASSO_F32, 2, 0, 8},    {LASSO_F32, 2, 0, 32},
 };
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
@@ -96,6 +98,7 @@ lasso_status lasso_batch_tune(const float* X, int64_t n, int64_t p, int64_t ldx,
     o.gemm_dtype = kCandidates[c].dtype;
     o.batch_ctas_per_sm = kCandidates[c].per_sm;
     o.gemm_tile_n = kCandidates[c].tile_n;
+    o.batch_group = kCandidates[c].group;
     for (int rep = 0; rep < 2 && status == LASSO_OK; ++rep) {
       if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) status = set_error(LASSO_ERR_CUDA, "event record failed");
       if (status == LASSO_OK)
@@ -103,6 +106,11 @@ lasso_status lasso_batch_tune(const float* X, int64_t n, int64_t p, int64_t ldx,
                              nullptr, stats, w + L.solver, L.beta, stream);
       if (status == LASSO_OK && rep == 1 && cudaEventRecord(e1, st) != cudaSuccess)
         status = set_error(LASSO_ERR_CUDA, "event record failed");
+    }
+    if (status == LASSO_ERR_INVALID_ARG && kCandidates[c].group > 1) {  // the group does not fit this GPU
+      status = LASSO_OK;
+      if (times_ms) times_ms[c] = -1.f;
+      continue;
     }
     if (status != LASSO_OK) break;
     float ms = 0.f;
@@ -123,6 +131,7 @@ lasso_status lasso_batch_tune(const float* X, int64_t n, int64_t p, int64_t ldx,
   tuned->gemm_dtype = kCandidates[best].dtype;
   tuned->batch_ctas_per_sm = kCandidates[best].per_sm;
   tuned->gemm_tile_n = kCandidates[best].tile_n;
+  tuned->batch_group = kCandidates[best].group;
   return LASSO_OK;
 }
 

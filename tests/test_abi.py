@@ -45,7 +45,7 @@ def test_default_opts(pkg):
     o = pkg.lasso_default_opts()
     assert (o.screen_period, o.dual_point, o.xtr_scope, o.warm_start) == (10, 0, 0, 1)
     assert o.max_epochs == 100000 and o.gap_tol_rel == 1e-6 and o.gemm_dtype == pkg.LASSO_BF16
-    assert (o.batch_ctas_per_sm, o.gemm_tile_n, o.reserved) == (0, 0, 0)
+    assert (o.batch_ctas_per_sm, o.gemm_tile_n, o.batch_group) == (0, 0, 0)
 
 
 def test_lambda_grid_matches_oracle(pkg):
@@ -96,7 +96,7 @@ def test_argument_errors(pkg, kw, status):
 @pytest.mark.parametrize("field,value", [("screen_period", 0), ("dual_point", 2), ("xtr_scope", -1),
                                          ("warm_start", 3), ("max_epochs", -1), ("gap_tol_rel", -1.0),
                                          ("gemm_dtype", 7), ("batch_ctas_per_sm", 3), ("gemm_tile_n", 96),
-                                         ("reserved", 1)])
+                                         ("batch_group", 65), ("batch_group", -1)])
 def test_option_errors(pkg, field, value):
     o = pkg.lasso_default_opts(**{field: value})
     with pytest.raises(pkg.LassoError) as e:
@@ -142,11 +142,20 @@ def test_lista_host_checks(pkg):
 
 def test_tune_host_checks(pkg):
     """The autotuner's sizes and arguments are checked on the host."""
-    assert pkg.lasso_batch_tune_candidates() == 6
+    assert pkg.lasso_batch_tune_candidates() == 8
     assert pkg.lasso_batch_tune_workspace_size(100, 1000, 0, 5) == 0
     assert pkg.lasso_batch_tune_workspace_size(100, 1000, 16, 5) >= 16 * 5 * 1000 * 8
     tuned = pkg.LassoOpts()
     with pytest.raises(pkg.LassoError) as e:  # sample > B
         pkg.lasso_batch_tune(None, 100, 1000, 100, None, 100, None, 0, 4, None, 10, None, 0, None, 8, 5, tuned,
                              None, None, 0, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+
+
+def test_batch_group_needs_fp32_checks(pkg):
+    """Groups of CTAs per problem run the per-CTA FP32 mode only."""
+    o = pkg.lasso_default_opts(batch_group=4)  # default gemm_dtype is LASSO_BF16
+    with pytest.raises(pkg.LassoError) as e:
+        pkg.lasso_batch(1 << 12, 10, 20, 12, 1 << 12, 10, None, 0, 2, 1 << 12, 3, None, 0, o, 1 << 12, None,
+                        1 << 12, 1 << 12, 1 << 20, None)
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG

@@ -202,7 +202,7 @@ def test_batch_captured_in_cuda_graph(pkg):
 
 
 def test_autotuner_picks_a_shape_and_keeps_results(pkg):
-    """lasso_batch_tune times its six launch shapes and returns the fastest;
+    """lasso_batch_tune times its eight launch shapes and returns the fastest;
     solving with the tuned options gives bit-identical coefficients, masks
     and pass counts to the default shape (every shape makes the FP64 test's
     decisions), and both match the oracle."""
@@ -215,11 +215,12 @@ def test_autotuner_picks_a_shape_and_keeps_results(pkg):
     r = torch.from_numpy(ratios).to(dev)
     base = pkg.lasso_default_opts(gap_tol_rel=1e-9)
     tuned, times = pkg.tune_batch(Xd, Yd, r, n=200, row_mask=Md, opts=base, sample=16, lambdas=4)
-    assert np.all(times > 0)
-    k = int(np.argmin(times))
-    shapes = [(pkg.LASSO_F32, 2, 0), (pkg.LASSO_F32, 1, 0), (pkg.LASSO_BF16, 2, 128), (pkg.LASSO_BF16, 1, 128),
-              (pkg.LASSO_BF16, 2, 256), (pkg.LASSO_BF16, 1, 256)]
-    assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n) == shapes[k]
+    assert np.all((times > 0) | (times == -1)) and np.any(times > 0)
+    k = int(np.argmin(np.where(times > 0, times, np.inf)))
+    shapes = [(pkg.LASSO_F32, 2, 0, 1), (pkg.LASSO_F32, 1, 0, 1), (pkg.LASSO_BF16, 2, 128, 1),
+              (pkg.LASSO_BF16, 1, 128, 1), (pkg.LASSO_BF16, 2, 256, 1), (pkg.LASSO_BF16, 1, 256, 1),
+              (pkg.LASSO_F32, 2, 0, 8), (pkg.LASSO_F32, 2, 0, 32)]
+    assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n, tuned.batch_group) == shapes[k]
     assert tuned.gap_tol_rel == 1e-9
     outs = {}
     for name, o in (("default", base), ("tuned", tuned)):
@@ -250,3 +251,26 @@ def test_batch_launch_shapes(pkg, per_sm, tile):
     g1 = run_gpu_batch(pkg, prob["XT"], 333, Y, rmask, ratios, gemm_dtype=pkg.LASSO_F32, batch_ctas_per_sm=per_sm,
                        **opt)
     check_batch(g1, o)
+
+
+@pytest.mark.parametrize("group", [2, 8, 32])
+def test_batch_groups_of_ctas(pkg, group):
+    """Several CTAs per problem (feature slices and a barrier per group) give
+    the oracle's results, with row subsets, starting points and a problem
+    whose response holds a NaN."""
+    prob, Y, rmask = _subsample_problem(211, 150, 3001, 11, correlated=True)
+    rng = np.random.default_rng(211)
+    beta0 = np.zeros((11, 3001))
+    for b in range(0, 11, 3):
+        idx = rng.choice(3001, size=15, replace=False)
+        beta0[b, idx] = 0.2 * rng.standard_normal(15)
+    Y[5, int(np.nonzero(rmask[5])[0][0])] = np.nan
+    ratios = oracle.lambda_ratios(9, 1.5)[1:]
+    opt = dict(gap_tol_rel=1e-9, xtr_scope=1)
+    g = run_gpu_batch(pkg, prob["XT"], 150, Y, rmask, ratios, beta0=beta0, gemm_dtype=pkg.LASSO_F32,
+                      batch_group=group, **opt)
+    assert np.all(g["stats"]["status"][5] == pkg.LASSO_ERR_NONFINITE)
+    keep = [b for b in range(11) if b != 5]
+    o = oracle.lasso_batch(prob["XT"], (Y * rmask)[keep], ratios, row_mask=rmask[keep], n=150, beta0=beta0[keep],
+                           **opt)
+    check_batch(dict(beta=g["beta"][keep], mask=g["mask"][keep], stats=g["stats"][keep]), o)
