@@ -50,20 +50,23 @@ def build(force: bool = False) -> str:
 class _Opts(ctypes.Structure):
     _fields_ = [("screen_period", ctypes.c_int32), ("dual_point", ctypes.c_int32),
                 ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double)]
+                ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
+                ("screen_rule", ctypes.c_int32)]
 
 
 class _CheckResult(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("xtr_inf", ctypes.c_double),
                 ("primal", ctypes.c_double), ("dual", ctypes.c_double),
                 ("gap", ctypes.c_double), ("radius", ctypes.c_double),
-                ("tau", ctypes.c_double), ("n_kept", ctypes.c_int64)]
+                ("tau", ctypes.c_double), ("n_kept", ctypes.c_int64),
+                ("dome_rad", ctypes.c_double), ("dome_alpha", ctypes.c_double)]
 
 
 class _Log(ctypes.Structure):
     _fields_ = [("cap", ctypes.c_int64), ("count", ctypes.c_int64),
                 ("t", ctypes.c_void_p), ("gap", ctypes.c_void_p), ("radius", ctypes.c_void_p),
-                ("alpha", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+                ("alpha", ctypes.c_void_p), ("rho", ctypes.c_void_p),
+                ("dome_rad", ctypes.c_void_p), ("dome_alpha", ctypes.c_void_p)]
 
 
 def _load():
@@ -82,8 +85,10 @@ def _bind(path):
     lib.orc_precompute.restype = None
     lib.orc_lambda_ratios.argtypes = [I32, D, P]
     lib.orc_lambda_ratios.restype = None
-    lib.orc_check.argtypes = [P, I64, I64, I64, P, D, P, P, P, P, D, P, P, P, P]
+    lib.orc_check.argtypes = [P, I64, I64, I64, P, D, P, P, P, P, P, D, P, P, P, P, P]
     lib.orc_check.restype = None
+    lib.orc_dome_support.argtypes = [D, D, D, D, D]
+    lib.orc_dome_support.restype = D
     lib.orc_cd_pass.argtypes = [P, I64, I64, P, I64, P, D, P, P]
     lib.orc_cd_pass.restype = None
     lib.orc_lasso_path.argtypes = [P, I64, I64, I64, P, P, I32, P, P, P, P, P, P]
@@ -112,9 +117,9 @@ def _colmajor64(X, n=None):
 
 
 def _opts(screen_period=10, dual_point=0, xtr_scope=0, warm_start=True, max_epochs=100000,
-          gap_tol_rel=1e-6):
+          gap_tol_rel=1e-6, screen_rule=0):
     return _Opts(int(screen_period), int(dual_point), int(xtr_scope), int(bool(warm_start)),
-                 int(max_epochs), float(gap_tol_rel))
+                 int(max_epochs), float(gap_tol_rel), int(screen_rule))
 
 
 def mask_words(p):
@@ -148,9 +153,16 @@ def lambda_ratios(T, delta):
     return out
 
 
+def dome_support(cx, rad, alpha, nx, xnorm):
+    """Support function of the dome D(c, rad, alpha, nrm) at x, from c^T x,
+    nrm^T x and ||x|| (appendix, dome test)."""
+    return _load().orc_dome_support(float(cx), float(rad), float(alpha), float(nx), float(xnorm))
+
+
 def check(X, y, beta, rho, lam, mask_in=None, n=None, **opt):
-    """One GAP SAFE check on given (beta, rho): returns dict with c, alpha,
-    xtr_inf, primal, dual, gap, radius, tau, n_kept and mask (uint32 words)."""
+    """One GAP SAFE check on given (beta, rho): returns dict with c, mu (the
+    test value per feature), alpha, xtr_inf, primal, dual, gap, radius, tau,
+    n_kept, dome_rad, dome_alpha and mask (uint32 words)."""
     lib = _load()
     Xc, n, p, ldx = _colmajor64(X, n)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -163,15 +175,16 @@ def check(X, y, beta, rho, lam, mask_in=None, n=None, **opt):
     mask_in = np.ascontiguousarray(mask_in, dtype=np.uint32)
     mask_out = np.empty(W, dtype=np.uint32)
     c = np.empty(p)
+    mu = np.empty(p)
     res = _CheckResult()
     o = _opts(**opt)
     beta = np.ascontiguousarray(beta, dtype=np.float64)
     rho = np.ascontiguousarray(rho, dtype=np.float64)
-    lib.orc_check(_ptr(Xc), n, p, ldx, _ptr(y), pre["ynorm2"], _ptr(pre["norms2"]), _ptr(beta),
-                  _ptr(rho), _ptr(mask_in), float(lam), ctypes.byref(o), _ptr(mask_out), _ptr(c),
-                  ctypes.byref(res))
+    lib.orc_check(_ptr(Xc), n, p, ldx, _ptr(y), pre["ynorm2"], _ptr(pre["norms2"]), _ptr(pre["c0"]),
+                  _ptr(beta), _ptr(rho), _ptr(mask_in), float(lam), ctypes.byref(o), _ptr(mask_out),
+                  _ptr(c), _ptr(mu), ctypes.byref(res))
     out = {f: getattr(res, f) for f, _ in _CheckResult._fields_}
-    out.update(c=c, mask=mask_out)
+    out.update(c=c, mu=mu, mask=mask_out)
     return out
 
 
@@ -210,8 +223,10 @@ def lasso_path(X, y, ratios, beta0=None, n=None, log_checks=0, **opt):
     if log_checks:
         cap = int(log_checks)
         logbufs = dict(t=np.zeros(cap, dtype=np.int32), gap=np.zeros(cap), radius=np.zeros(cap),
-                       alpha=np.zeros(cap), rho=np.zeros((cap, n)))
-        log = _Log(cap, 0, *(_ptr(logbufs[k]).value for k in ("t", "gap", "radius", "alpha", "rho")))
+                       alpha=np.zeros(cap), rho=np.zeros((cap, n)), dome_rad=np.zeros(cap),
+                       dome_alpha=np.zeros(cap))
+        log = _Log(cap, 0, *(_ptr(logbufs[k]).value
+                             for k in ("t", "gap", "radius", "alpha", "rho", "dome_rad", "dome_alpha")))
     rc = lib.orc_lasso_path(_ptr(Xc), n, p, ldx, _ptr(y), _ptr(ratios), T, _ptr(b0), ctypes.byref(o),
                             _ptr(beta_out), _ptr(mask_out), _ptr(stats),
                             ctypes.byref(log) if log is not None else None)

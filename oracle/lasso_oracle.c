@@ -42,6 +42,23 @@
  *       unchanged, so the certified gap belongs to the returned beta.
  *   R9  lambda_t = lambda_max * 10^(-delta t / (T-1)), t = 0..T-1 (Sec. 3.3),
  *       passed in as the ratios lambda_t / lambda_max.
+ *   R10 GAP SAFE dome (screen_rule == 1, Eq. (11) with the parameters of the
+ *       appendix): ball center (y/lambda + theta)/2, ball radius R/2 with
+ *       R = ||y/lambda - theta||, unit normal (y/lambda - theta)/R and ratio
+ *       alpha_D = 2 r^2/R^2 - 1, where r^2 = (||y||^2 - ||X beta - y||^2 -
+ *       2 lambda ||beta||_1)/lambda^2 is the radius of Thm. 2 taken from the
+ *       primal point beta (clipped at 0).  The main text prints the normal
+ *       with the opposite sign; the appendix's sign is the one for which the
+ *       dome contains theta_hat (theta_hat is in the ball with diameter
+ *       [theta, y/lambda] because it is the projection of y/lambda on the
+ *       dual feasible set, and at distance >= r from y/lambda because
+ *       D(theta_hat) <= P(beta)).  As for the sphere, the rounding bound tau of
+ *       R7 enlarges the dome: lambda^2 R^2 is taken as ||lambda theta - y||^2
+ *       + tau and lambda^2 r^2 as ||y||^2 - 2P - tau.  A feature is screened
+ *       when the sphere test or the dome test screens it (both regions are
+ *       safe; in exact arithmetic the dome lies inside the sphere, so this is
+ *       the dome test).  When theta = y/lambda the dome is a point and only
+ *       the sphere test runs.
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,6 +80,7 @@ typedef struct {
   int32_t warm_start;    /* 1: beta carried from the previous lambda */
   int64_t max_epochs;    /* K, passes per lambda */
   double gap_tol_rel;    /* eps / ||y||^2 */
+  int32_t screen_rule;   /* 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome (R10) */
 } orc_opts;
 
 typedef struct {
@@ -74,6 +92,8 @@ typedef struct {
   double radius;   /* sqrt(2 (max(gap,0) + tau)) / lambda, Prop. 1 / Eq. (10) */
   double tau;      /* rounding inflation of the gap used in the radius (R7) */
   int64_t n_kept;  /* features kept by the test */
+  double dome_rad;   /* dome ball radius (R10; 0 when the dome is not used) */
+  double dome_alpha; /* dome ratio alpha_D (R10) */
 } orc_check_result;
 
 static int mask_get(const uint32_t* m, int64_t j) { return (m[j >> 5] >> (j & 31)) & 1u; }
@@ -109,16 +129,33 @@ void orc_lambda_ratios(int32_t T, double delta, double* ratios) {
     ratios[t] = (T == 1) ? 1.0 : pow(10.0, -delta * (double)t / (double)(T - 1));
 }
 
+/* Support function of the dome D(c, rad, alpha, nrm) (appendix, dome test)
+ * at a vector x, from the scalars c^T x, nrm^T x and ||x||: the dome is the
+ * part of the ball B(c, rad) on the side nrm^T (z - c) <= -alpha rad of its
+ * hyperplane.  If x points far enough against nrm, the ball's own extreme
+ * point c + rad x/||x|| lies in the dome; otherwise the maximum is on the
+ * circle where the hyperplane cuts the sphere. */
+double orc_dome_support(double cx, double rad, double alpha, double nx, double xnorm) {
+  if (nx < -alpha * xnorm) return cx + rad * xnorm;
+  double w = xnorm * xnorm - nx * nx;
+  if (w < 0.0) w = 0.0;
+  return cx - rad * alpha * nx + rad * sqrt(w * (1.0 - alpha * alpha));
+}
+
 /* One GAP SAFE check (Algorithm 1, the "every f passes" block):
  * c = X_scope^T rho, dual point theta (Eq. (8) / R2), P, D, gap, radius
  * r = sqrt(2 G)/lambda (Prop. 1), sphere test |x_j^T theta| + r ||x_j|| >= 1
- * (Eq. (7), Eq. (10)) applied to the kept features of mask_in.
+ * (Eq. (7), Eq. (10)) applied to the kept features of mask_in; with
+ * screen_rule == 1 also the dome test max(sigma(x_j), sigma(-x_j)) >= 1
+ * (Eq. (11), R10), which needs c0 = X^T y.
  * Reads beta and rho, changes neither.  c (length p, may be NULL) receives
- * x_j^T rho for the scope (0 outside it). */
+ * x_j^T rho for the scope (0 outside it); mu (length p, may be NULL) receives
+ * the test value of each feature of mask_in (the sphere's, or the dome's when
+ * the dome runs) and 0 elsewhere. */
 void orc_check(const double* X, int64_t n, int64_t p, int64_t ldx, const double* y, double yy,
-               const double* norms2, const double* beta, const double* rho,
+               const double* norms2, const double* c0, const double* beta, const double* rho,
                const uint32_t* mask_in, double lambda, const orc_opts* o,
-               uint32_t* mask_out, double* c, orc_check_result* res) {
+               uint32_t* mask_out, double* c, double* mu_out, orc_check_result* res) {
   int64_t words = (p + 31) / 32;
   double* cbuf = c ? c : (double*)malloc(sizeof(double) * (size_t)p);
   double m = 0.0;
@@ -161,12 +198,40 @@ void orc_check(const double* X, int64_t n, int64_t p, int64_t ldx, const double*
   double r = sqrt(2.0 * Gs) / lambda;
   double aa = fabs(alpha);
 
+  /* dome parameters (R10) */
+  int dome = o->screen_rule == 1 && d2 > 0.0;
+  double drad = 0.0, dal = 0.0, dR = 0.0;
+  if (dome) {
+    double big = d2 + tau;                 /* lambda^2 R^2, enlarged */
+    double small = yy - 2.0 * P - tau;     /* lambda^2 r^2, reduced */
+    if (small < 0.0) small = 0.0;
+    double q = small / big;
+    if (q > 1.0) q = 1.0;
+    dal = 2.0 * q - 1.0;
+    drad = 0.5 * sqrt(big) / lambda;
+    dR = sqrt(d2) / lambda;                /* ||y/lambda - theta||, scales the normal */
+  }
+
   memcpy(mask_out, mask_in, (size_t)words * sizeof(uint32_t));
   int64_t kept = 0;
   for (int64_t j = 0; j < p; ++j) {
+    if (mu_out) mu_out[j] = 0.0;
     if (!mask_get(mask_in, j)) continue;
-    double mu = fabs(cbuf[j]) * aa + r * sqrt(norms2[j]);
-    if (mu < 1.0) mask_clear(mask_out, j);
+    double xn = sqrt(norms2[j]);
+    double mu = fabs(cbuf[j]) * aa + r * xn;
+    int screen = mu < 1.0;
+    if (dome) {
+      double xt = alpha * cbuf[j];         /* x_j^T theta */
+      double xy = c0[j] / lambda;          /* x_j^T y / lambda */
+      double cx = 0.5 * (xy + xt);         /* x_j^T (dome center) */
+      double nx = (xy - xt) / dR;          /* x_j^T (unit normal) */
+      double sp = orc_dome_support(cx, drad, dal, nx, xn);
+      double sm = orc_dome_support(-cx, drad, dal, -nx, xn);
+      mu = sp > sm ? sp : sm;
+      if (mu < 1.0) screen = 1;
+    }
+    if (mu_out) mu_out[j] = mu;
+    if (screen) mask_clear(mask_out, j);
     else ++kept;
   }
   if (!c) free(cbuf);
@@ -178,6 +243,8 @@ void orc_check(const double* X, int64_t n, int64_t p, int64_t ldx, const double*
   res->radius = r;
   res->tau = tau;
   res->n_kept = kept;
+  res->dome_rad = drad;
+  res->dome_alpha = dal;
 }
 
 /* One cyclic pass of Algorithm 1 over the ascending list of kept features:
@@ -204,7 +271,8 @@ void orc_cd_pass(const double* X, int64_t n, int64_t ldx, const int64_t* list, i
 }
 
 /* Check log for the safety tests (may be NULL): per check, the lambda index,
- * gap, radius, alpha and the residual rho of that check (n values). */
+ * gap, radius, alpha, the residual rho of that check (n values) and the
+ * dome's radius and ratio (R10). */
 typedef struct {
   int64_t cap;      /* capacity in checks */
   int64_t count;    /* checks written */
@@ -213,6 +281,8 @@ typedef struct {
   double* radius;   /* cap */
   double* alpha;    /* cap */
   double* rho;      /* cap * n */
+  double* dome_rad;   /* cap */
+  double* dome_alpha; /* cap */
 } orc_log;
 
 /* Algorithm 1 (CD with GAP SAFE rules) over the grid lambda_t = lambda_max *
@@ -262,7 +332,7 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
     int converged = 0;
     orc_check_result cr;
     for (;;) {
-      orc_check(X, n, p, ldx, y, yy, norms2, beta, rho, mask, lambda, o, mask2, NULL, &cr);
+      orc_check(X, n, p, ldx, y, yy, norms2, c0, beta, rho, mask, lambda, o, mask2, NULL, NULL, &cr);
       ++checks;
       if (log && log->count < log->cap) {
         int64_t k = log->count++;
@@ -271,6 +341,8 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
         log->radius[k] = cr.radius;
         log->alpha[k] = cr.alpha;
         memcpy(log->rho + k * n, rho, sizeof(double) * (size_t)n);
+        log->dome_rad[k] = cr.dome_rad;
+        log->dome_alpha[k] = cr.dome_alpha;
       }
       /* newly screened features whose coefficient is nonzero (R8) */
       if (cr.gap <= eps) {

@@ -12,6 +12,7 @@ import tempfile
 import pytest
 
 import oracle
+import tests.test_oracle_dome as dome
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lasso_oracle.c")
@@ -28,7 +29,7 @@ MUTANTS = [
     ("threshold uses norm not squared norm", "double thr = lambda / n2;", "double thr = lambda / sqrt(n2);"),
     ("check correlates y instead of rho", "double cj = in_scope ? dot_col(X, ldx, n, j, rho) : 0.0;",
      "double cj = in_scope ? dot_col(X, ldx, n, j, y) : 0.0;"),
-    ("sphere test reversed", "if (mu < 1.0) mask_clear(mask_out, j);", "if (mu > 1.0) mask_clear(mask_out, j);"),
+    ("sphere test reversed", "int screen = mu < 1.0;", "int screen = mu > 1.0;"),
     ("radius divided twice by lambda", "double r = sqrt(2.0 * Gs) / lambda;",
      "double r = sqrt(2.0 * Gs) / (lambda * lambda);"),
     ("radius without gap", "double Gs = (G > 0.0 ? G : 0.0) + tau;", "double Gs = tau;"),
@@ -42,6 +43,15 @@ MUTANTS = [
     ("Eq. (8) clipped to the wrong side", "if (a < -lim) a = -lim;", "if (a < -lim) a = lim;"),
     ("lambda_max from the smallest correlation", "if (fabs(c0[j]) > lmax) { lmax = fabs(c0[j]); arg = j; }",
      "if (j == 0 || fabs(c0[j]) < lmax) { lmax = fabs(c0[j]); arg = j; }"),
+    # the dome test (Eq. (11), appendix)
+    ("dome normal with the main text's sign", "double nx = (xy - xt) / dR;", "double nx = (xt - xy) / dR;"),
+    ("dome ratio with the opposite sign", "dal = 2.0 * q - 1.0;", "dal = 1.0 - 2.0 * q;"),
+    ("dome radius R instead of R/2", "drad = 0.5 * sqrt(big) / lambda;", "drad = sqrt(big) / lambda;"),
+    ("dome support case condition", "if (nx < -alpha * xnorm) return", "if (nx < alpha * xnorm) return"),
+    ("dome center without theta", "double cx = 0.5 * (xy + xt);", "double cx = 0.5 * xy;"),
+    ("dome ratio from the gap instead of r(beta)", "double small = yy - 2.0 * P - tau;",
+     "double small = 2.0 * G;"),
+    ("dome rim term without (1 - alpha^2)", "sqrt(w * (1.0 - alpha * alpha))", "sqrt(w)"),
 ]
 
 PIN_CALLS = [
@@ -59,6 +69,11 @@ PIN_CALLS = [
     (pins.test_finite_identification, {}),
     (pins.test_prop3_sequential_identity, {}),
     (pins.test_dual_point_eq8_is_projection_on_span, {}),
+    (dome.test_dome_support_matches_sampled_maximum, {"alpha": 0.35}),
+    (dome.test_dome_value_is_the_maximum_over_the_safe_set, {}),
+    (dome.test_dome_lies_inside_the_sphere, {}),
+    (dome.test_every_dome_contains_dual_optimum, {}),
+    (dome.test_dome_path_reaches_the_exact_solution, {"seed": 44, "n": 20, "p": 8}),
 ]
 
 
