@@ -61,6 +61,8 @@ def _args():
                          "solver solutions, then solve 1024 held-out responses from zero and from the net")
     ap.add_argument("--plain-sample", type=int, default=8,
                     help="problems of the batched workload timed one at a time on the plain path")
+    ap.add_argument("--screen-rule", type=int, choices=[0, 1], default=0,
+                    help="0: GAP SAFE sphere (default); 1: sphere and GAP SAFE dome")
     return ap.parse_args()
 
 
@@ -86,9 +88,9 @@ def aggregate_ranks(total_ms, solves, device=None):
     return float(t.item()), int(round(float(s.item())))
 
 
-def _workload():
+def _workload(screen_rule=0):
     import gen
-    return gen.workload2()
+    return dict(gen.workload2(), screen_rule=screen_rule)
 
 
 def _config(w):
@@ -96,6 +98,7 @@ def _config(w):
                         f"beta* 50-sparse N(0,1), SNR 5, T={w['T']} geometric grid lambda_max..lambda_max/1000, "
                         f"check every {w['f']} passes, gap<=1e-6*||y||^2",
             "n": w["n"], "p": w["p"], "T": w["T"], "screen_period": w["f"], "gap_tol_rel": w["tol"],
+            "screen_rule": "dome" if w.get("screen_rule", 0) == 1 else "sphere",
             "l2": "flushed (512 MiB write) before every timed step",
             "parallelism": "replicas (one independent path per GPU)"}
 
@@ -106,7 +109,8 @@ def _oracle_sample(w, T=CPU_SAMPLE_T):
     oracle.build()
     ratios = oracle.lambda_ratios(w["T"], w["delta"])[:T]
     t0 = time.perf_counter()
-    out = oracle.lasso_path(w["XT"], w["y"], ratios, n=w["n"], screen_period=w["f"], gap_tol_rel=w["tol"])
+    out = oracle.lasso_path(w["XT"], w["y"], ratios, n=w["n"], screen_period=w["f"], gap_tol_rel=w["tol"],
+                            screen_rule=w.get("screen_rule", 0))
     dt = time.perf_counter() - t0
     return int((out["stats"]["converged"] == 1).sum()), dt
 
@@ -197,7 +201,7 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    w = _workload()
+    w = _workload(args.screen_rule)
     for _ in range(args.warmup):
         _oracle_sample(w)
     total_s, total_solves, times = 0.0, 0, []
@@ -234,7 +238,7 @@ def run_ours(args):
     build()
     import paper_1505_03410_gb300 as pkg
 
-    w = _workload()
+    w = _workload(args.screen_rule)
     n, p, T = w["n"], w["p"], w["T"]
     ratios_h = pkg.lasso_lambda_grid(T, w["delta"])
     if 0 < args.lambdas < T:
@@ -244,7 +248,7 @@ def run_ours(args):
     XT = torch.from_numpy(w["XT"]).to(dev)
     y = torch.from_numpy(w["y"]).to(dev)
     ratios = torch.from_numpy(ratios_h).to(dev)
-    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"])
+    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=args.screen_rule)
     words = (p + 31) // 32
     beta_out = torch.empty((T, p), dtype=torch.float64, device=dev)
     mask_out = torch.empty((T, words), dtype=torch.int32, device=dev)

@@ -75,6 +75,11 @@ typedef struct lasso_opts {
                             the single path does; for designs that do not fit L2 it spreads each
                             problem's column reads over several SMs.  lasso_batch_tune picks this,
                             batch_ctas_per_sm, gemm_tile_n and gemm_dtype */
+  int32_t screen_rule;   /* 0: GAP SAFE sphere, Eq. (10) (default); 1: sphere and GAP SAFE dome,
+                            Eq. (11) with the appendix's parameters: a feature is screened when
+                            either test screens it.  The dome lies inside the sphere, so it screens
+                            at least as much; each check then evaluates x_j^T rho exactly for the
+                            features the sphere keeps */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */

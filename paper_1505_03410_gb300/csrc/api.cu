@@ -44,6 +44,7 @@ lasso_status check_opts(const lasso_opts& o) {
     return set_error(LASSO_ERR_INVALID_ARG, "batch_group must lie in [0, 64]");
   if (o.batch_group > 1 && o.gemm_dtype != LASSO_F32)
     return set_error(LASSO_ERR_INVALID_ARG, "batch_group > 1 needs gemm_dtype = LASSO_F32");
+  if (o.screen_rule != 0 && o.screen_rule != 1) return set_error(LASSO_ERR_INVALID_ARG, "screen_rule must be 0 or 1");
   return LASSO_OK;
 }
 

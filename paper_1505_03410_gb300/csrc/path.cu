@@ -73,6 +73,7 @@ struct Args {
   int s_cap;        // max chain entries per round
   int f;            // screen period
   int dual_point, xtr_scope, warm_start;
+  int screen_rule;  // 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome
   long long max_epochs;
   const double* y;
   const double* ratios;
@@ -84,7 +85,7 @@ struct Args {
   size_t cta_bytes;
   size_t o_ctrl, o_cnt_kept, o_cnt_sup, o_cnt_nnz, o_cnt_zero, o_part_l1, o_nrm, o_nrmf, o_ftab, o_bdf, o_b0df,
       o_rho_h, o_rho_l, o_rho0_h, o_rho0_l, o_ctil, o_mask, o_A, o_sup0, o_sup1, o_chain, o_entered, o_oldb, o_recs,
-      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb, o_sk, o_mref, o_msnap;
+      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb, o_sk, o_mref, o_msnap, o_cy;
   // batched solver: B problems over the same X, problem b uses column b of Y
   // (ld ldy) and the rows i with rmask[i + b * ldm] != 0 (all rows if null)
   int B;
@@ -148,6 +149,20 @@ __device__ __forceinline__ uint32_t chain_row_bits(const Args& a, int b) {
 constexpr int kBatchRowsPerThread = 8;
 static_assert(kBatchRowsPerThread * kThreads >= kMaxRows, "a thread's rows must cover n <= kMaxRows");
 
+// Support function of the dome D(c, rad, al, nrm) at a vector x, from c^T x,
+// nrm^T x and ||x|| (the paper's appendix, dome test).  The dome is the part
+// of the ball B(c, rad) with nrm^T (z - c) <= -al rad.  When x points far
+// enough against nrm the ball's extreme point c + rad x/||x|| lies in the
+// dome; otherwise the maximum is on the circle where the hyperplane cuts the
+// sphere.
+__device__ __forceinline__ double dome_support(double xc, double rad, double al, double xnr, double xn) {
+  if (xnr < __dmul_rn(-al, xn)) return __dadd_rn(xc, __dmul_rn(rad, xn));
+  double w = __dsub_rn(__dmul_rn(xn, xn), __dmul_rn(xnr, xnr));
+  if (w < 0.0) w = 0.0;
+  return __dadd_rn(__dsub_rn(xc, __dmul_rn(__dmul_rn(rad, al), xnr)),
+                   __dmul_rn(rad, __dsqrt_rn(__dmul_rn(w, __dsub_rn(1.0, __dmul_rn(al, al))))));
+}
+
 // Per-problem set-up of a batched problem (the single path does this with the
 // precompute kernels): y restricted to the problem's rows, rho = y - X beta0,
 // ||y||^2, and for every column the norm over those rows and x_j^T y, whose
@@ -170,6 +185,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
   float4* ftab = reinterpret_cast<float4*>(wsb + a.o_ftab);
   float2* bdf = reinterpret_cast<float2*>(wsb + a.o_bdf);
   float2* b0df = reinterpret_cast<float2*>(wsb + a.o_b0df);
+  double* cy = reinterpret_cast<double*>(wsb + a.o_cy);
   if (reset) {
     if (tid == 0) {
       ctl->err = 0;
@@ -219,6 +235,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
       const double nr = __dsqrt_rn(s2);
       nrm[j] = nr;
       nrmf[j] = __double2float_ru(nr);
+      cy[j] = sy;
       const df2 iv = df_from_double(s2 > 0.0 ? __drcp_rn(s2) : 0.0);
       ftab[j] = make_float4(iv.h, iv.l, 0.f, 0.f);
       if (isfinite(sy)) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(fabs(sy)));
@@ -545,6 +562,24 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
       const double Gs = (Gap > 0.0 ? Gap : 0.0) + tau;
       const double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
       const double aa = fabs(alpha);
+      // GAP SAFE dome (Eq. (11), parameters of the appendix): center
+      // (y/lambda + theta)/2, radius R/2 with R = ||y/lambda - theta||, unit
+      // normal (y/lambda - theta)/R, ratio 2 r^2/R^2 - 1 with r the radius of
+      // Thm. 2 from the primal point; lambda^2 R^2 is enlarged and lambda^2 r^2
+      // reduced by the rounding bound tau, as the sphere's gap is.  When
+      // theta = y/lambda the dome is a point and only the sphere runs.
+      const bool dome = a.screen_rule == 1 && d2 > 0.0;
+      double drad = 0.0, dal = 0.0, dR = 1.0;
+      if (dome) {
+        const double big = __dadd_rn(d2, tau);
+        double small = __dsub_rn(__dsub_rn(yy, __dmul_rn(2.0, P)), tau);
+        if (small < 0.0) small = 0.0;
+        double q = __ddiv_rn(small, big);
+        if (q > 1.0) q = 1.0;
+        dal = __dsub_rn(__dmul_rn(2.0, q), 1.0);
+        drad = __ddiv_rn(__dmul_rn(0.5, __dsqrt_rn(big)), lam);
+        dR = __ddiv_rn(__dsqrt_rn(d2), lam);
+      }
       ++checks;
       xcols += scope_n;
       const bool stop = Gap <= vload(ctl->eps);
@@ -569,19 +604,33 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
             const float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
             const float clo = fmaxf(__fsub_rd(fabsf(c), E), 0.f);
             const float mu_lo = __fadd_rd(__fmul_rd(clo, aaf_lo), __fmul_rd(radf_lo, nfl));
+            // a feature the sphere screens for certain is screened by the
+            // dome too (the dome lies inside the sphere); any other one gets
+            // the exact evaluation when the dome runs
             if (mu_hi < 0.999999f) keep = false;
-            else if (mu_lo >= 1.000001f) keep = true;
+            else if (mu_lo >= 1.000001f && !dome) keep = true;
             else amb = true;
           }
-          // exact decision for the undecided ones, as the FP64 test of Eq. (7)
+          // exact decision for the undecided ones, as the FP64 tests of
+          // Eq. (7) (sphere) and Eq. (11) (dome)
           unsigned ambm = __ballot_sync(0xffffffffu, amb);
           while (ambm) {
             const int l = __ffs(ambm) - 1;
             ambm &= ambm - 1;
             const int jj = w0 + l;
             const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldcg(WS(float, nrmf) + jj), rnormf));
-            const double mu = __dadd_rn(__dmul_rn(fabs(df_to_double(ce)), aa), __dmul_rn(rad, __ldcg(WS(double, nrm) + jj)));
-            if (lane == l) keep = !(mu < 1.0);
+            const double cj = df_to_double(ce), xn = __ldcg(WS(double, nrm) + jj);
+            const double mu = __dadd_rn(__dmul_rn(fabs(cj), aa), __dmul_rn(rad, xn));
+            bool kp = !(mu < 1.0);
+            if (dome) {
+              const double xt = __dmul_rn(alpha, cj);                       // x_j^T theta
+              const double xy = __ddiv_rn(__ldcg(WS(double, cy) + jj), lam);  // x_j^T y / lambda
+              const double xc = __dmul_rn(0.5, __dadd_rn(xy, xt));          // x_j^T center
+              const double xnr = __ddiv_rn(__dsub_rn(xy, xt), dR);          // x_j^T normal
+              const double md = fmax(dome_support(xc, drad, dal, xnr, xn), dome_support(-xc, drad, dal, -xnr, xn));
+              if (md < 1.0) kp = false;
+            }
+            if (lane == l) keep = kp;
           }
           const float2 bj = valid ? ld_beta(cx, j) : make_float2(0.f, 0.f);
           bool nz = nonzero2(bj);
@@ -1091,11 +1140,12 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
 
 // ---------------------------------------------------------------- setup kernels
 // ||x_j||, 1/||x_j||^2, c0_j = x_j^T y -> lambda_max = ||X^T y||_inf (Sec. 1.2),
-// finiteness of X, split planes of an FP64 X, beta0 in double-float.
+// finiteness of X, split planes of an FP64 X, beta0 in double-float.  c0 is
+// kept for the dome test.
 template <typename XT>
 __global__ void precompute_kernel(const XT* X, long long ldx, int n, int p, const double* y, const double* beta0,
                                   float* Xh, float* Xl, long long ldh, double* nrm, float* nrmf, float4* ftab,
-                                  float2* bdf, float2* b0df, Ctrl* ctl) {
+                                  float2* bdf, float2* b0df, double* cy, Ctrl* ctl) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = warp; j < p; j += nwarps) {
@@ -1126,6 +1176,7 @@ __global__ void precompute_kernel(const XT* X, long long ldx, int n, int p, cons
       const double nr = __dsqrt_rn(s2);
       nrm[j] = nr;
       nrmf[j] = __double2float_ru(nr);
+      cy[j] = sy;
       const df2 iv = df_from_double(s2 > 0.0 ? __drcp_rn(s2) : 0.0);
       ftab[j] = make_float4(iv.h, iv.l, 0.f, 0.f);
       if (isfinite(sy)) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(fabs(sy)));
@@ -1270,7 +1321,7 @@ struct Layout {
 enum {
   L_ctrl, L_cnt, L_part_l1, L_nrm, L_nrmf, L_ftab, L_bdf, L_b0df, L_rho_h, L_rho_l, L_rho0_h, L_rho0_l, L_ctil,
   L_mask, L_A, L_sup0, L_sup1, L_chain, L_entered, L_oldb, L_recs, L_snap, L_zl_j, L_zl_b, L_zbits, L_yb, L_sk,
-  L_mref, L_msnap, L_N
+  L_mref, L_msnap, L_cy, L_N
 };
 
 Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
@@ -1312,6 +1363,7 @@ Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
   take(L_sk, sizeof(float) * p);
   take(L_mref, sizeof(float) * p);
   take(L_msnap, sizeof(float) * (s_cap + 2));
+  take(L_cy, sizeof(double) * p);
   L.region = off;
   L.planes = planes ? 2 * align256(sizeof(float) * (size_t)ldw * (size_t)p) : 0;
   L.total = L.region + L.planes;
@@ -1353,6 +1405,7 @@ void set_offsets(Args& a, const Layout& L) {
   a.o_sk = L.o[L_sk];
   a.o_mref = L.o[L_mref];
   a.o_msnap = L.o[L_msnap];
+  a.o_cy = L.o[L_cy];
   a.ldw = L.ldw;
   a.s_cap = L.s_cap;
 }
@@ -1398,6 +1451,7 @@ void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) 
   a.words = (int)((p + 31) / 32);
   a.f = o.screen_period;
   a.dual_point = o.dual_point;
+  a.screen_rule = o.screen_rule;
   a.xtr_scope = o.xtr_scope;
   a.warm_start = o.warm_start;
   a.max_epochs = o.max_epochs;
@@ -1497,6 +1551,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
   float4* ftab = reinterpret_cast<float4*>(base + a.o_ftab);
   float2* bdf = reinterpret_cast<float2*>(base + a.o_bdf);
   float2* b0df = reinterpret_cast<float2*>(base + a.o_b0df);
+  double* cy = reinterpret_cast<double*>(base + a.o_cy);
   float* rho_h = reinterpret_cast<float*>(base + a.o_rho_h);
   float* rho_l = reinterpret_cast<float*>(base + a.o_rho_l);
   float* rho0_h = reinterpret_cast<float*>(base + a.o_rho0_h);
@@ -1504,10 +1559,10 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
   const int blocks = d.sms * 8;
   if (f64)
     precompute_kernel<double><<<blocks, 256, 0, stream>>>(static_cast<const double*>(X), ldx, (int)n, (int)p, y, beta0,
-                                                          Xh_w, Xl_w, a.ldw, nrm, nrmf, ftab, bdf, b0df, ctrl);
+                                                          Xh_w, Xl_w, a.ldw, nrm, nrmf, ftab, bdf, b0df, cy, ctrl);
   else
     precompute_kernel<float><<<blocks, 256, 0, stream>>>(static_cast<const float*>(X), ldx, (int)n, (int)p, y, beta0,
-                                                         nullptr, nullptr, a.ldw, nrm, nrmf, ftab, bdf, b0df, ctrl);
+                                                         nullptr, nullptr, a.ldw, nrm, nrmf, ftab, bdf, b0df, cy, ctrl);
   CUDA_TRY(cudaGetLastError());
   const int rb = (int)std::min<long long>(a.ldw, (long long)d.sms * 4);
   if (f64)

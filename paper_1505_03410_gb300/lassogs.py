@@ -46,7 +46,8 @@ class LassoOpts(ctypes.Structure):
                 ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
                 ("gemm_dtype", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
-                ("gemm_tile_n", ctypes.c_int32), ("batch_group", ctypes.c_int32)]
+                ("gemm_tile_n", ctypes.c_int32), ("batch_group", ctypes.c_int32),
+                ("screen_rule", ctypes.c_int32)]
 
 
 class LassoPathStats(ctypes.Structure):

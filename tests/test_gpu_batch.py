@@ -274,3 +274,16 @@ def test_batch_groups_of_ctas(pkg, group):
     o = oracle.lasso_batch(prob["XT"], (Y * rmask)[keep], ratios, row_mask=rmask[keep], n=150, beta0=beta0[keep],
                            **opt)
     check_batch(dict(beta=g["beta"][keep], mask=g["mask"][keep], stats=g["stats"][keep]), o)
+
+
+@pytest.mark.parametrize("gemm,group", [(1, 1), (2, 1), (1, 8)])
+def test_batch_dome(pkg, gemm, group):
+    """GAP SAFE dome (Eq. (11)) in every batched mode: per-CTA FP32 checks,
+    lockstep split-BF16 first checks and groups of CTAs; x_j^T y is taken on
+    each problem's own rows."""
+    prob, Y, rmask = _subsample_problem(207, 150, 1100, 6, correlated=True)
+    ratios = oracle.lambda_ratios(10, 2.0)
+    opt = dict(gap_tol_rel=1e-9, screen_rule=1)
+    g = run_gpu_batch(pkg, prob["XT"], 150, Y, rmask, ratios, gemm_dtype=gemm, batch_group=group, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=150, **opt)
+    check_batch(g, o)

@@ -103,6 +103,34 @@ def test_options_parity(pkg, opt):
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("seed,n,p,dtype,corr,opt", [
+    (121, 77, 1537, np.float32, True, {}),
+    (122, 37, 300, np.float64, False, {}),
+    (123, 500, 2500, np.float32, True, {}),
+    (124, 130, 3000, np.float32, True, dict(dual_point=1)),
+    (125, 90, 1200, np.float32, True, dict(xtr_scope=1, screen_period=3)),
+])
+def test_dome_parity(pkg, seed, n, p, dtype, corr, opt):
+    """GAP SAFE dome (Eq. (11), screen_rule = 1): masks, supports, pass and
+    check counts, objectives and coefficients equal the oracle's run with the
+    same rule, alone and with the other options."""
+    prob = gen.small_problem(seed, n, p, dtype=dtype, k=max(2, min(n, p) // 20), noise=0.2, correlated=corr)
+    ratios = oracle.lambda_ratios(14, 2.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-9, screen_rule=1, **opt)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-9, screen_rule=1, **opt)
+    assert_parity(g, o)
+
+
+def test_dome_workload2_prefix(pkg):
+    """The dome on the Toeplitz 500 x 50000 FP32 path in the benchmark's launch
+    configuration: the first 20 lambdas match the oracle element by element."""
+    w = gen.workload2()
+    ratios = oracle.lambda_ratios(w["T"], w["delta"])[:20]
+    g = run_gpu(pkg, w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=1)
+    o = run_orc(w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=1)
+    assert_parity(g, o)
+
+
 def test_beta0_and_screened_nonzero(pkg):
     """A warm start with nonzero coefficients on inactive features exercises
     the removal of screened nonzero coefficients (Remark 3)."""
