@@ -42,7 +42,7 @@
  *       unchanged, so the certified gap belongs to the returned beta.
  *   R9  lambda_t = lambda_max * 10^(-delta t / (T-1)), t = 0..T-1 (Sec. 3.3),
  *       passed in as the ratios lambda_t / lambda_max.
- *   R10 GAP SAFE dome (screen_rule == 1, Eq. (11) with the parameters of the
+ *   R14 GAP SAFE dome (screen_rule == 1, Eq. (11) with the parameters of the
  *       appendix): ball center (y/lambda + theta)/2, ball radius R/2 with
  *       R = ||y/lambda - theta||, unit normal (y/lambda - theta)/R and ratio
  *       alpha_D = 2 r^2/R^2 - 1, where r^2 = (||y||^2 - ||X beta - y||^2 -
@@ -80,7 +80,7 @@ typedef struct {
   int32_t warm_start;    /* 1: beta carried from the previous lambda */
   int64_t max_epochs;    /* K, passes per lambda */
   double gap_tol_rel;    /* eps / ||y||^2 */
-  int32_t screen_rule;   /* 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome (R10) */
+  int32_t screen_rule;   /* 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome (R14) */
 } orc_opts;
 
 typedef struct {
@@ -92,8 +92,8 @@ typedef struct {
   double radius;   /* sqrt(2 (max(gap,0) + tau)) / lambda, Prop. 1 / Eq. (10) */
   double tau;      /* rounding inflation of the gap used in the radius (R7) */
   int64_t n_kept;  /* features kept by the test */
-  double dome_rad;   /* dome ball radius (R10; 0 when the dome is not used) */
-  double dome_alpha; /* dome ratio alpha_D (R10) */
+  double dome_rad;   /* dome ball radius (R14; 0 when the dome is not used) */
+  double dome_alpha; /* dome ratio alpha_D (R14) */
 } orc_check_result;
 
 static int mask_get(const uint32_t* m, int64_t j) { return (m[j >> 5] >> (j & 31)) & 1u; }
@@ -147,7 +147,7 @@ double orc_dome_support(double cx, double rad, double alpha, double nx, double x
  * r = sqrt(2 G)/lambda (Prop. 1), sphere test |x_j^T theta| + r ||x_j|| >= 1
  * (Eq. (7), Eq. (10)) applied to the kept features of mask_in; with
  * screen_rule == 1 also the dome test max(sigma(x_j), sigma(-x_j)) >= 1
- * (Eq. (11), R10), which needs c0 = X^T y.
+ * (Eq. (11), R14), which needs c0 = X^T y.
  * Reads beta and rho, changes neither.  c (length p, may be NULL) receives
  * x_j^T rho for the scope (0 outside it); mu (length p, may be NULL) receives
  * the test value of each feature of mask_in (the sphere's, or the dome's when
@@ -198,7 +198,7 @@ void orc_check(const double* X, int64_t n, int64_t p, int64_t ldx, const double*
   double r = sqrt(2.0 * Gs) / lambda;
   double aa = fabs(alpha);
 
-  /* dome parameters (R10) */
+  /* dome parameters (R14) */
   int dome = o->screen_rule == 1 && d2 > 0.0;
   double drad = 0.0, dal = 0.0, dR = 0.0;
   if (dome) {
@@ -272,7 +272,7 @@ void orc_cd_pass(const double* X, int64_t n, int64_t ldx, const int64_t* list, i
 
 /* Check log for the safety tests (may be NULL): per check, the lambda index,
  * gap, radius, alpha, the residual rho of that check (n values) and the
- * dome's radius and ratio (R10). */
+ * dome's radius and ratio (R14). */
 typedef struct {
   int64_t cap;      /* capacity in checks */
   int64_t count;    /* checks written */
