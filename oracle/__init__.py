@@ -51,7 +51,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("screen_period", ctypes.c_int32), ("dual_point", ctypes.c_int32),
                 ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
-                ("screen_rule", ctypes.c_int32)]
+                ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32)]
 
 
 class _CheckResult(ctypes.Structure):
@@ -117,9 +117,9 @@ def _colmajor64(X, n=None):
 
 
 def _opts(screen_period=10, dual_point=0, xtr_scope=0, warm_start=True, max_epochs=100000,
-          gap_tol_rel=1e-6, screen_rule=0):
+          gap_tol_rel=1e-6, screen_rule=0, refined_radius=0):
     return _Opts(int(screen_period), int(dual_point), int(xtr_scope), int(bool(warm_start)),
-                 int(max_epochs), float(gap_tol_rel), int(screen_rule))
+                 int(max_epochs), float(gap_tol_rel), int(screen_rule), int(refined_radius))
 
 
 def mask_words(p):

@@ -59,6 +59,13 @@
  *       safe; in exact arithmetic the dome lies inside the sphere, so this is
  *       the dome test).  When theta = y/lambda the dome is a point and only
  *       the sphere test runs.
+ *   R15 refined radius (refined_radius == 1, Thm. 2): the sphere's radius is
+ *       min(sqrt(2 (G + tau))/lambda, R), with lambda^2 R^2 = ||lambda theta -
+ *       y||^2 + tau.  Thm. 2's radius sqrt(R^2 - r(beta)^2) equals sqrt(2 G) /
+ *       lambda when ||y||^2 - 2P >= 0 (expand G = P - D) and equals R when the
+ *       clipped r(beta) is 0, i.e. for iterates whose primal value exceeds
+ *       P(0) = ||y||^2/2; the minimum is that radius with the rounding bound
+ *       of R7 on both arguments.
  */
 #include <math.h>
 #include <stdint.h>
@@ -81,6 +88,7 @@ typedef struct {
   int64_t max_epochs;    /* K, passes per lambda */
   double gap_tol_rel;    /* eps / ||y||^2 */
   int32_t screen_rule;   /* 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome (R14) */
+  int32_t refined_radius; /* 1: the sphere radius of Thm. 2 (R15) */
 } orc_opts;
 
 typedef struct {
@@ -89,7 +97,7 @@ typedef struct {
   double primal;   /* P_lambda(beta), Eq. (1) */
   double dual;     /* D_lambda(theta), Eq. (2) */
   double gap;      /* P - D */
-  double radius;   /* sqrt(2 (max(gap,0) + tau)) / lambda, Prop. 1 / Eq. (10) */
+  double radius;   /* sqrt(2 (max(gap,0) + tau)) / lambda, Prop. 1 / Eq. (10); Thm. 2's with R15 */
   double tau;      /* rounding inflation of the gap used in the radius (R7) */
   int64_t n_kept;  /* features kept by the test */
   double dome_rad;   /* dome ball radius (R14; 0 when the dome is not used) */
@@ -196,6 +204,10 @@ void orc_check(const double* X, int64_t n, int64_t p, int64_t ldx, const double*
   double tau = 2.0 * (double)(n + p + 8) * u * (rr + lambda * l1 + yy + d2);
   double Gs = (G > 0.0 ? G : 0.0) + tau;
   double r = sqrt(2.0 * Gs) / lambda;
+  if (o->refined_radius == 1) {
+    double Rt = sqrt(d2 + tau) / lambda;   /* ||theta - y/lambda||, enlarged (R15) */
+    if (Rt < r) r = Rt;
+  }
   double aa = fabs(alpha);
 
   /* dome parameters (R14) */

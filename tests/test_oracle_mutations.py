@@ -52,6 +52,10 @@ MUTANTS = [
     ("dome ratio from the gap instead of r(beta)", "double small = yy - 2.0 * P - tau;",
      "double small = 2.0 * G;"),
     ("dome rim term without (1 - alpha^2)", "sqrt(w * (1.0 - alpha * alpha))", "sqrt(w)"),
+    # the refined radius of Thm. 2
+    ("refined radius always R", "if (Rt < r) r = Rt;", "r = Rt;"),
+    ("refined radius from the gap term", "double Rt = sqrt(d2 + tau) / lambda;",
+     "double Rt = sqrt(2.0 * Gs) / (lambda * lambda);"),
 ]
 
 PIN_CALLS = [
@@ -69,6 +73,7 @@ PIN_CALLS = [
     (pins.test_finite_identification, {}),
     (pins.test_prop3_sequential_identity, {}),
     (pins.test_dual_point_eq8_is_projection_on_span, {}),
+    (pins.test_refined_radius_of_thm2, {}),
     (dome.test_dome_support_matches_sampled_maximum, {"alpha": 0.35}),
     (dome.test_dome_value_is_the_maximum_over_the_safe_set, {}),
     (dome.test_dome_lies_inside_the_sphere, {}),

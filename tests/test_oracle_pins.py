@@ -171,6 +171,47 @@ def test_every_sphere_contains_dual_optimum(orc):
         assert d <= log["radius"][k] * (1 + 1e-9) + 1e-12, (k, t, d, log["radius"][k])
 
 
+def test_refined_radius_of_thm2(orc):
+    """Thm. 2 + Prop. 1 (refined_radius = 1): theta_hat lies in
+    B(theta, (R^2 - r(beta)^2)^(1/2)) with R = ||theta - y/lambda|| and
+    r(beta) = (||y||^2 - ||X beta - y||^2 - 2 lambda ||beta||_1)_+^(1/2) / lambda,
+    and that radius is at most sqrt(2 G)/lambda.  Runs from a poor start
+    (P(beta0) > P(0) at every lambda, warm starts off) so that the clipped
+    r(beta) = 0 case occurs and the radius is strictly smaller there; the
+    path still reaches the exact brute-force solution."""
+    prob = _problem(21, 15, 10, k=3, noise=0.2)
+    X, y = _dense(prob), prob["y"]
+    rng = np.random.default_rng(21)
+    beta0 = 3.0 * rng.standard_normal(10)
+    ratios = orc.lambda_ratios(5, 1.5)[1:]
+    out = orc.lasso_path(X, y, ratios, beta0=beta0, warm_start=False, gap_tol_rel=1e-13,
+                         log_checks=5000, screen_period=1, refined_radius=1)
+    lmax = out["lambda_max"]
+    sols = {t: lasso_bruteforce(X, y, lmax * ratios[t])[0] for t in range(len(ratios))}
+    log = out["log"]
+    strict = 0
+    for k in range(len(log["t"])):
+        t = int(log["t"][k])
+        lam = lmax * ratios[t]
+        theta = log["alpha"][k] * log["rho"][k]
+        R2 = np.sum((theta - y / lam) ** 2)
+        D = 0.5 * y @ y - 0.5 * lam ** 2 * R2             # Eq. (2)
+        P = log["gap"][k] + D
+        r2 = max(0.0, y @ y - 2 * P) / lam ** 2           # r(beta)^2, clipped
+        thm2 = np.sqrt(max(R2 - r2, 0.0))
+        gap_r = np.sqrt(2 * max(log["gap"][k], 0.0)) / lam
+        # equal up to the rounding inflation of the gap (far below 1e-12 ||y||^2)
+        assert abs(log["radius"][k] ** 2 - thm2 ** 2) <= 1e-7 * thm2 ** 2 + 1e-12 * (y @ y) / lam ** 2, \
+            (k, log["radius"][k], thm2)
+        assert log["radius"][k] ** 2 <= gap_r ** 2 * (1 + 1e-9) + 1e-12 * (y @ y) / lam ** 2
+        theta_hat = (y - X @ sols[t]) / lam
+        assert np.linalg.norm(theta - theta_hat) <= log["radius"][k] * (1 + 1e-9) + 1e-12
+        strict += log["radius"][k] < 0.99 * gap_r
+    assert strict > 0
+    for t in range(len(ratios)):
+        np.testing.assert_allclose(out["beta"][t], sols[t], atol=1e-6)
+
+
 def test_screened_features_are_zero(orc):
     """Eq. (5): a feature the test screens has beta_hat_j = 0 -- checked
     against the exact brute-force solution and the tight CD output."""
