@@ -80,6 +80,10 @@ typedef struct lasso_opts {
                             either test screens it.  The dome lies inside the sphere, so it screens
                             at least as much; each check then evaluates x_j^T rho exactly for the
                             features the sphere keeps */
+  int32_t refined_radius; /* 0: sphere radius sqrt(2 gap)/lambda, Eq. (10) (default); 1: the radius
+                            of Thm. 2, (R^2 - r(beta)^2)^(1/2) with R = ||theta - y/lambda||, which
+                            is the smaller of sqrt(2 gap)/lambda and R; it differs only for iterates
+                            whose primal value exceeds P(0) = ||y||^2/2 (a poor starting point) */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */

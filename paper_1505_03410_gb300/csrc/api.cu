@@ -45,6 +45,8 @@ lasso_status check_opts(const lasso_opts& o) {
   if (o.batch_group > 1 && o.gemm_dtype != LASSO_F32)
     return set_error(LASSO_ERR_INVALID_ARG, "batch_group > 1 needs gemm_dtype = LASSO_F32");
   if (o.screen_rule != 0 && o.screen_rule != 1) return set_error(LASSO_ERR_INVALID_ARG, "screen_rule must be 0 or 1");
+  if (o.refined_radius != 0 && o.refined_radius != 1)
+    return set_error(LASSO_ERR_INVALID_ARG, "refined_radius must be 0 or 1");
   return LASSO_OK;
 }
 

@@ -74,6 +74,7 @@ struct Args {
   int f;            // screen period
   int dual_point, xtr_scope, warm_start;
   int screen_rule;  // 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome
+  int refined_radius;  // 1: the sphere radius of Thm. 2
   long long max_epochs;
   const double* y;
   const double* ratios;
@@ -560,7 +561,13 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
       const double Gap = __dsub_rn(P, D);
       const double tau = 2.0 * (double)(a.n + a.p + 8) * u64 * (rr + lam * l1 + yy + d2);
       const double Gs = (Gap > 0.0 ? Gap : 0.0) + tau;
-      const double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
+      double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
+      if (a.refined_radius == 1) {
+        // Thm. 2's radius (R^2 - r(beta)^2)^(1/2): sqrt(2 G)/lambda, or R =
+        // ||theta - y/lambda|| when the clipped r(beta) is 0 (P > ||y||^2/2)
+        const double Rt = __ddiv_rn(__dsqrt_rn(__dadd_rn(d2, tau)), lam);
+        if (Rt < rad) rad = Rt;
+      }
       const double aa = fabs(alpha);
       // GAP SAFE dome (Eq. (11), parameters of the appendix): center
       // (y/lambda + theta)/2, radius R/2 with R = ||y/lambda - theta||, unit
@@ -1452,6 +1459,7 @@ void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) 
   a.f = o.screen_period;
   a.dual_point = o.dual_point;
   a.screen_rule = o.screen_rule;
+  a.refined_radius = o.refined_radius;
   a.xtr_scope = o.xtr_scope;
   a.warm_start = o.warm_start;
   a.max_epochs = o.max_epochs;

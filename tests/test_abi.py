@@ -45,7 +45,7 @@ def test_default_opts(pkg):
     o = pkg.lasso_default_opts()
     assert (o.screen_period, o.dual_point, o.xtr_scope, o.warm_start) == (10, 0, 0, 1)
     assert o.max_epochs == 100000 and o.gap_tol_rel == 1e-6 and o.gemm_dtype == pkg.LASSO_BF16
-    assert (o.batch_ctas_per_sm, o.gemm_tile_n, o.batch_group, o.screen_rule) == (0, 0, 0, 0)
+    assert (o.batch_ctas_per_sm, o.gemm_tile_n, o.batch_group, o.screen_rule, o.refined_radius) == (0, 0, 0, 0, 0)
 
 
 def test_lambda_grid_matches_oracle(pkg):
@@ -96,7 +96,8 @@ def test_argument_errors(pkg, kw, status):
 @pytest.mark.parametrize("field,value", [("screen_period", 0), ("dual_point", 2), ("xtr_scope", -1),
                                          ("warm_start", 3), ("max_epochs", -1), ("gap_tol_rel", -1.0),
                                          ("gemm_dtype", 7), ("batch_ctas_per_sm", 3), ("gemm_tile_n", 96),
-                                         ("batch_group", 65), ("batch_group", -1), ("screen_rule", 2)])
+                                         ("batch_group", 65), ("batch_group", -1), ("screen_rule", 2),
+                                         ("refined_radius", 2)])
 def test_option_errors(pkg, field, value):
     o = pkg.lasso_default_opts(**{field: value})
     with pytest.raises(pkg.LassoError) as e:

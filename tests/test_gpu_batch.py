@@ -287,3 +287,17 @@ def test_batch_dome(pkg, gemm, group):
     g = run_gpu_batch(pkg, prob["XT"], 150, Y, rmask, ratios, gemm_dtype=gemm, batch_group=group, **opt)
     o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=150, **opt)
     check_batch(g, o)
+
+
+@pytest.mark.parametrize("gemm", GEMM)
+def test_batch_refined_radius(pkg, gemm):
+    """Thm. 2's radius in the batched modes, from poor per-problem starting
+    points (warm starts off, grids below lambda_max)."""
+    prob, Y, rmask = _subsample_problem(208, 120, 700, 4)
+    rng = np.random.default_rng(208)
+    beta0 = 2.0 * rng.standard_normal((4, 700)) * (rng.random((4, 700)) < 0.05)
+    ratios = oracle.lambda_ratios(7, 1.5)[1:]
+    opt = dict(gap_tol_rel=1e-9, refined_radius=1, warm_start=0)
+    g = run_gpu_batch(pkg, prob["XT"], 120, Y, rmask, ratios, beta0=beta0, gemm_dtype=gemm, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=120, beta0=beta0, **opt)
+    check_batch(g, o)

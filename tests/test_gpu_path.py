@@ -131,6 +131,21 @@ def test_dome_workload2_prefix(pkg):
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("opt", [dict(refined_radius=1), dict(refined_radius=1, screen_rule=1)])
+def test_refined_radius_parity(pkg, opt):
+    """Thm. 2's radius (refined_radius = 1) from a poor start: P(beta0) is far
+    above P(0) at every lambda and warm starts are off, so the first check of
+    each lambda uses R = ||theta - y/lambda||, several times smaller than
+    sqrt(2 gap)/lambda there."""
+    prob = gen.small_problem(126, 80, 900, dtype=np.float64, k=4, noise=0.2)
+    rng = np.random.default_rng(126)
+    beta0 = 2.0 * rng.standard_normal(900) * (rng.random(900) < 0.05)
+    ratios = oracle.lambda_ratios(8, 1.5)[1:]
+    g = run_gpu(pkg, prob, ratios, beta0=beta0, warm_start=0, gap_tol_rel=1e-9, **opt)
+    o = run_orc(prob, ratios, beta0=beta0, warm_start=0, gap_tol_rel=1e-9, **opt)
+    assert_parity(g, o)
+
+
 def test_beta0_and_screened_nonzero(pkg):
     """A warm start with nonzero coefficients on inactive features exercises
     the removal of screened nonzero coefficients (Remark 3)."""
