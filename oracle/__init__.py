@@ -51,7 +51,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("screen_period", ctypes.c_int32), ("dual_point", ctypes.c_int32),
                 ("xtr_scope", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
-                ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32)]
+                ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32),
+                ("enet_alpha", ctypes.c_double)]
 
 
 class _CheckResult(ctypes.Structure):
@@ -117,9 +118,10 @@ def _colmajor64(X, n=None):
 
 
 def _opts(screen_period=10, dual_point=0, xtr_scope=0, warm_start=True, max_epochs=100000,
-          gap_tol_rel=1e-6, screen_rule=0, refined_radius=0):
+          gap_tol_rel=1e-6, screen_rule=0, refined_radius=0, enet_alpha=1.0):
     return _Opts(int(screen_period), int(dual_point), int(xtr_scope), int(bool(warm_start)),
-                 int(max_epochs), float(gap_tol_rel), int(screen_rule), int(refined_radius))
+                 int(max_epochs), float(gap_tol_rel), int(screen_rule), int(refined_radius),
+                 float(enet_alpha))
 
 
 def mask_words(p):
@@ -232,7 +234,8 @@ def lasso_path(X, y, ratios, beta0=None, n=None, log_checks=0, **opt):
                             ctypes.byref(log) if log is not None else None)
     pre = precompute(Xc, y, n=n)
     out = dict(beta=beta_out, mask=mask_out, stats={f: stats[:, i] for i, f in enumerate(STAT_FIELDS)},
-               status=int(rc), lambda_max=pre["lambda_max"], ynorm2=pre["ynorm2"])
+               status=int(rc), lambda_max=pre["lambda_max"] / float(opt.get("enet_alpha", 1.0)),
+               ynorm2=pre["ynorm2"])
     if log is not None:
         k = log.count
         out["log"] = {key: v[:k] for key, v in logbufs.items()}

@@ -66,6 +66,17 @@
  *       clipped r(beta) is 0, i.e. for iterates whose primal value exceeds
  *       P(0) = ||y||^2/2; the minimum is that radius with the rounding bound
  *       of R7 on both arguments.
+ *   R16 Elastic-Net (enet_alpha < 1, the paper's appendix on the Elastic-Net):
+ *       minimise 1/2 ||X beta - y||^2 + lambda a ||beta||_1 + lambda (1 - a)/2
+ *       ||beta||^2 (a = enet_alpha) as the Lasso with penalty a lambda on the
+ *       augmented design [X; sqrt((1 - a) lambda) I] and response [y; 0].  The
+ *       augmented design changes with lambda, so it is built at every lambda
+ *       and the whole of Algorithm 1 (checks, screening, passes) runs on it.
+ *       lambda_max = ||X^T y||_inf / a (beta = 0 is optimal from there on).  The
+ *       residual's first n entries are carried between lambdas as in the
+ *       Lasso; its last p entries are -sqrt((1 - a) lambda) beta at the new
+ *       lambda.  The stats report lambda (not a lambda) and the objectives of
+ *       the augmented Lasso, which are the Elastic-Net's.
  */
 #include <math.h>
 #include <stdint.h>
@@ -89,6 +100,7 @@ typedef struct {
   double gap_tol_rel;    /* eps / ||y||^2 */
   int32_t screen_rule;   /* 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome (R14) */
   int32_t refined_radius; /* 1: the sphere radius of Thm. 2 (R15) */
+  double enet_alpha;     /* a in (0, 1]: 1 is the Lasso, below 1 the Elastic-Net (R16) */
 } orc_opts;
 
 typedef struct {
@@ -306,9 +318,18 @@ typedef struct {
 int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const double* y,
                    const double* ratios, int32_t T, const double* beta0, const orc_opts* o,
                    double* beta_out, uint32_t* mask_out, double* stats, orc_log* log) {
-  if (n <= 0 || p <= 0 || ldx < n || T <= 0 || o->screen_period <= 0 || o->max_epochs < 0)
+  if (n <= 0 || p <= 0 || ldx < n || T <= 0 || o->screen_period <= 0 || o->max_epochs < 0 ||
+      !(o->enet_alpha > 0.0 && o->enet_alpha <= 1.0))
     return ORC_ERR_INVALID;
   int64_t words = (p + 31) / 32;
+  /* Elastic-Net (R16): the augmented design, response, residual and tables */
+  int enet = o->enet_alpha < 1.0;
+  int64_t na = n + p;
+  double* Xa = enet ? (double*)malloc(sizeof(double) * (size_t)(na * p)) : NULL;
+  double* ya = enet ? (double*)malloc(sizeof(double) * (size_t)na) : NULL;
+  double* rhoa = enet ? (double*)malloc(sizeof(double) * (size_t)na) : NULL;
+  double* norms2a = enet ? (double*)malloc(sizeof(double) * (size_t)p) : NULL;
+  double* c0a = enet ? (double*)malloc(sizeof(double) * (size_t)p) : NULL;
   double* norms2 = (double*)malloc(sizeof(double) * (size_t)p);
   double* c0 = (double*)malloc(sizeof(double) * (size_t)p);
   double* beta = (double*)malloc(sizeof(double) * (size_t)p);
@@ -318,7 +339,7 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
   uint32_t* mask2 = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)words);
   double scal[3];
   orc_precompute(X, n, p, ldx, y, norms2, c0, scal);
-  double lmax = scal[0], yy = scal[1];
+  double lmax = scal[0] / o->enet_alpha, yy = scal[1];
   double eps = o->gap_tol_rel * yy;
   int status = ORC_OK;
 
@@ -340,11 +361,43 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
     for (int64_t w = 0; w < words; ++w) mask[w] = 0xffffffffu;
     if (p % 32) mask[words - 1] = (1u << (p % 32)) - 1u;
 
+    /* the design this lambda's Lasso runs on, and its L1 penalty */
+    const double* Xs = X;
+    int64_t ns = n, lds = ldx;
+    const double* ys = y;
+    double* rs = rho;
+    const double* n2s = norms2;
+    const double* c0s = c0;
+    double lam1 = lambda;
+    if (enet) {
+      double mu = (1.0 - o->enet_alpha) * lambda;
+      double sm = sqrt(mu);
+      lam1 = o->enet_alpha * lambda;
+      for (int64_t j = 0; j < p; ++j) {
+        double* col = Xa + j * na;
+        for (int64_t i = 0; i < n; ++i) col[i] = X[i + j * ldx];
+        for (int64_t i = 0; i < p; ++i) col[n + i] = (i == j) ? sm : 0.0;
+      }
+      for (int64_t i = 0; i < n; ++i) ya[i] = y[i];
+      for (int64_t i = 0; i < p; ++i) ya[n + i] = 0.0;
+      for (int64_t i = 0; i < n; ++i) rhoa[i] = rho[i];
+      for (int64_t j = 0; j < p; ++j) rhoa[n + j] = -(sm * beta[j]);
+      double scal_a[3];
+      orc_precompute(Xa, na, p, na, ya, norms2a, c0a, scal_a);
+      Xs = Xa;
+      ns = na;
+      lds = na;
+      ys = ya;
+      rs = rhoa;
+      n2s = norms2a;
+      c0s = c0a;
+    }
+
     int64_t epochs = 0, checks = 0;
     int converged = 0;
     orc_check_result cr;
     for (;;) {
-      orc_check(X, n, p, ldx, y, yy, norms2, c0, beta, rho, mask, lambda, o, mask2, NULL, NULL, &cr);
+      orc_check(Xs, ns, p, lds, ys, yy, n2s, c0s, beta, rs, mask, lam1, o, mask2, NULL, NULL, &cr);
       ++checks;
       if (log && log->count < log->cap) {
         int64_t k = log->count++;
@@ -352,7 +405,7 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
         log->gap[k] = cr.gap;
         log->radius[k] = cr.radius;
         log->alpha[k] = cr.alpha;
-        memcpy(log->rho + k * n, rho, sizeof(double) * (size_t)n);
+        memcpy(log->rho + k * n, rs, sizeof(double) * (size_t)n);
         log->dome_rad[k] = cr.dome_rad;
         log->dome_alpha[k] = cr.dome_alpha;
       }
@@ -369,7 +422,7 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
       for (int64_t j = 0; j < p; ++j) {
         if (mask_get(mask, j) && !mask_get(mask2, j) && beta[j] != 0.0) {
           double b = beta[j];
-          for (int64_t i = 0; i < n; ++i) rho[i] += b * X[i + j * ldx];
+          for (int64_t i = 0; i < ns; ++i) rs[i] += b * Xs[i + j * lds];
           beta[j] = 0.0;
         }
       }
@@ -378,10 +431,12 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
       for (int64_t j = 0; j < p; ++j)
         if (mask_get(mask, j)) list[q++] = j;
       for (int32_t e = 0; e < o->screen_period && epochs < o->max_epochs; ++e) {
-        orc_cd_pass(X, n, ldx, list, q, norms2, lambda, beta, rho);
+        orc_cd_pass(Xs, ns, lds, list, q, n2s, lam1, beta, rs);
         ++epochs;
       }
     }
+    if (enet)
+      for (int64_t i = 0; i < n; ++i) rho[i] = rhoa[i];
     if (!converged) status = ORC_ERR_NOT_CONVERGED;
     int64_t nnz = 0;
     for (int64_t j = 0; j < p; ++j) {
@@ -403,6 +458,7 @@ int orc_lasso_path(const double* X, int64_t n, int64_t p, int64_t ldx, const dou
     s[ST_CONVERGED] = (double)converged;
   }
   free(norms2); free(c0); free(beta); free(rho); free(list); free(mask); free(mask2);
+  free(Xa); free(ya); free(rhoa); free(norms2a); free(c0a);
   return status;
 }
 

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 import tests.test_oracle_dome as dome
+import tests.test_oracle_enet as enet
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lasso_oracle.c")
@@ -38,7 +39,7 @@ MUTANTS = [
      "pow(10.0, -delta * (double)(t + 1) / (double)(T - 1))"),
     ("column stride transposed", "const double* x = X + j * ldx;\n  double s = 0.0;",
      "const double* x = X + j;\n  double s = 0.0;"),
-    ("screened coefficient not removed from residual", "for (int64_t i = 0; i < n; ++i) rho[i] += b * X[i + j * ldx];",
+    ("screened coefficient not removed from residual", "for (int64_t i = 0; i < ns; ++i) rs[i] += b * Xs[i + j * lds];",
      "(void)b;"),
     ("Eq. (8) clipped to the wrong side", "if (a < -lim) a = -lim;", "if (a < -lim) a = lim;"),
     ("lambda_max from the smallest correlation", "if (fabs(c0[j]) > lmax) { lmax = fabs(c0[j]); arg = j; }",
@@ -56,6 +57,13 @@ MUTANTS = [
     ("refined radius always R", "if (Rt < r) r = Rt;", "r = Rt;"),
     ("refined radius from the gap term", "double Rt = sqrt(d2 + tau) / lambda;",
      "double Rt = sqrt(2.0 * Gs) / (lambda * lambda);"),
+    # the Elastic-Net on the augmented design
+    ("Elastic-Net without the ridge rows", "col[n + i] = (i == j) ? sm : 0.0;", "col[n + i] = 0.0;"),
+    ("Elastic-Net lambda_max not divided by a", "double lmax = scal[0] / o->enet_alpha", "double lmax = scal[0]"),
+    ("Elastic-Net L1 penalty lambda instead of a lambda", "lam1 = o->enet_alpha * lambda;", "lam1 = lambda;"),
+    ("Elastic-Net ridge weight a lambda", "double mu = (1.0 - o->enet_alpha) * lambda;",
+     "double mu = o->enet_alpha * lambda;"),
+    ("Elastic-Net residual tail left at zero", "rhoa[n + j] = -(sm * beta[j]);", "rhoa[n + j] = 0.0;"),
 ]
 
 PIN_CALLS = [
@@ -79,6 +87,10 @@ PIN_CALLS = [
     (dome.test_dome_lies_inside_the_sphere, {}),
     (dome.test_every_dome_contains_dual_optimum, {}),
     (dome.test_dome_path_reaches_the_exact_solution, {"seed": 44, "n": 20, "p": 8}),
+    (enet.test_enet_orthonormal_closed_form, {"a": 0.3}),
+    (enet.test_enet_first_feature_enters, {}),
+    (enet.test_enet_bruteforce_agreement, {"seed": 32, "n": 20, "p": 8, "a": 0.5}),
+    (enet.test_enet_kkt_at_tight_solution, {}),
 ]
 
 
@@ -102,7 +114,11 @@ def test_mutant_is_caught(workdir, monkeypatch, name, orig, mut):
                            "-o", so, cpath, "-lm"])
     monkeypatch.setattr(oracle, "_lib", oracle._bind(so))
     caught = None
-    for fn, kw in PIN_CALLS:
+    # the pins of the mutated part run first (only the order changes: every
+    # pin still runs until one fails)
+    topic = "dome" if "dome" in name else "enet" if "Elastic" in name else "refined" if "refined" in name else ""
+    calls = sorted(PIN_CALLS, key=lambda c: 0 if topic and topic in c[0].__name__ else 1)
+    for fn, kw in calls:
         try:
             fn(oracle, **kw)
         except Exception as e:  # noqa: BLE001 -- any failure of a pin counts
