@@ -84,6 +84,12 @@ typedef struct lasso_opts {
                             of Thm. 2, (R^2 - r(beta)^2)^(1/2) with R = ||theta - y/lambda||, which
                             is the smaller of sqrt(2 gap)/lambda and R; it differs only for iterates
                             whose primal value exceeds P(0) = ||y||^2/2 (a poor starting point) */
+  double enet_alpha;     /* a in (0, 1]: 1 is the Lasso (default).  Below 1, lasso_path solves the
+                            Elastic-Net 1/2 ||X beta - y||^2 + lambda a ||beta||_1
+                            + lambda (1 - a)/2 ||beta||^2 (the paper's appendix) as the Lasso on
+                            [X; sqrt((1 - a) lambda) I], [y; 0] with penalty a lambda, the augmented
+                            rows implicit; lambda_max = ||X^T y||_inf / a and the stats report lambda.
+                            Needs an FP32 design and screen_rule = 0; lasso_batch requires 1 */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */

@@ -241,9 +241,10 @@ __device__ __forceinline__ void stage_column(const Ctx& a, float4* ring, int s, 
 // shared-memory exchange between warps otherwise.  Writes the new
 // coefficients to bdf, the old ones to oldb and the residual after entry c to
 // snapshot c + 1.
-template <int NGC, int CW, bool XLO, typename Ctx>
+template <int NGC, int CW, bool XLO, bool EN = false, typename Ctx>
 __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, int nc, float rho_bound,
-                          float4 (&rh)[NGC], float4 (&rl)[NGC], uint32_t row_bits = 0xffffffffu) {
+                          float4 (&rh)[NGC], float4 (&rl)[NGC], uint32_t row_bits = 0xffffffffu,
+                          df2 ridge = df2{0.f, 0.f}) {
   static_assert(CW >= 1 && CW <= kChainWarps, "chain warps");
   constexpr int CT = 32 * CW;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -336,8 +337,10 @@ __device__ void run_chain(const Ctx& a, ChainSmem& cs, float4* ring, int* jl, in
 #pragma unroll
         for (int w = 1; w < CW; ++w) Tl = limbs_add(Tl, cs.red[e & 1][w]);
       }
-      const df2 g = limbs_to_df(Tl, isc);
+      df2 g = limbs_to_df(Tl, isc);
       const df2 beta{r0.b.x, r0.b.y};
+      // Elastic-Net: the augmented column's correlation x_j^T rho - mu beta_j
+      if constexpr (EN) g = df_sub(g, df_mul(ridge, beta));
       df2 nb, d;
       cd_update(g, beta, r0.tab, nb, d);
       if (tid == 0) {
@@ -413,9 +416,12 @@ __device__ __forceinline__ void store_rho_regs(const Ctx& a, float* h, float* l,
 
 // Bound on ||rho|| for every iterate of a round: CD does not increase
 // P = 1/2 ||rho||^2 + lambda ||beta||_1 and only the chain coefficients move,
-// so ||rho_k||^2 <= ||rho_0||^2 + 2 lambda sum_chain |beta_c|.  Rounded up.
-template <int NGC, typename Ctx>
-__device__ float rho_bound_from_regs(const Ctx& a, const float4 (&rh)[NGC], double lam, int nc, float* fbuf) {
+// so ||rho_k||^2 <= ||rho_0||^2 + 2 lambda sum_chain |beta_c|.  With the
+// Elastic-Net's ridge term (mu/2) ||beta||^2 in P the bound gains
+// mu sum_chain beta_c^2.  Rounded up.
+template <int NGC, bool EN = false, typename Ctx>
+__device__ float rho_bound_from_regs(const Ctx& a, const float4 (&rh)[NGC], double lam, int nc, float* fbuf,
+                                     double ridge = 0.0) {
   const int tid = threadIdx.x;
   float ss = 0.f;
 #pragma unroll
@@ -426,28 +432,34 @@ __device__ float rho_bound_from_regs(const Ctx& a, const float4 (&rh)[NGC], doub
     ss = __fmaf_ru(v.z, v.z, ss);
     ss = __fmaf_ru(v.w, v.w, ss);
   }
-  float l1 = 0.f;
+  float l1 = 0.f, l2 = 0.f;
   for (int c = tid; c < nc; c += kThreads) {
     const float2 b = ld_beta(a, __ldcg(a.A + __ldcg(a.chain + c)));
-    l1 = __fadd_ru(l1, __fmul_ru(fabsf(b.x), 1.0001f));
+    const float ab = __fmul_ru(fabsf(b.x), 1.0001f);
+    l1 = __fadd_ru(l1, ab);
+    if constexpr (EN) l2 = __fmaf_ru(ab, ab, l2);
   }
   for (int o = 16; o > 0; o >>= 1) {
     ss = __fadd_ru(ss, __shfl_xor_sync(0xffffffffu, ss, o));
     l1 = __fadd_ru(l1, __shfl_xor_sync(0xffffffffu, l1, o));
+    if constexpr (EN) l2 = __fadd_ru(l2, __shfl_xor_sync(0xffffffffu, l2, o));
   }
   __syncthreads();
   if ((tid & 31) == 0) {
     fbuf[tid >> 5] = ss;
     fbuf[8 + (tid >> 5)] = l1;
+    if constexpr (EN) fbuf[16 + (tid >> 5)] = l2;
   }
   __syncthreads();
-  float S = 0.f, L = 0.f;
+  float S = 0.f, L = 0.f, L2 = 0.f;
   for (int w = 0; w < kThreads / 32; ++w) {
     S = __fadd_ru(S, fbuf[w]);
     L = __fadd_ru(L, fbuf[8 + w]);
+    if constexpr (EN) L2 = __fadd_ru(L2, fbuf[16 + w]);
   }
   __syncthreads();
-  const float P2 = __fadd_ru(S, __fmul_ru(__fmul_ru(2.0f, __double2float_ru(lam)), L));
+  float P2 = __fadd_ru(S, __fmul_ru(__fmul_ru(2.0f, __double2float_ru(lam)), L));
+  if constexpr (EN) P2 = __fadd_ru(P2, __fmul_ru(__double2float_ru(ridge), L2));
   return __fmul_ru(__fsqrt_ru(P2), 1.001f) + 1e-30f;
 }
 

@@ -75,6 +75,7 @@ struct Args {
   int dual_point, xtr_scope, warm_start;
   int screen_rule;  // 0: GAP SAFE sphere; 1: sphere and GAP SAFE dome
   int refined_radius;  // 1: the sphere radius of Thm. 2
+  double enet_alpha;   // Elastic-Net mixing a (1 = the Lasso)
   long long max_epochs;
   const double* y;
   const double* ratios;
@@ -86,7 +87,7 @@ struct Args {
   size_t cta_bytes;
   size_t o_ctrl, o_cnt_kept, o_cnt_sup, o_cnt_nnz, o_cnt_zero, o_part_l1, o_nrm, o_nrmf, o_ftab, o_bdf, o_b0df,
       o_rho_h, o_rho_l, o_rho0_h, o_rho0_l, o_ctil, o_mask, o_A, o_sup0, o_sup1, o_chain, o_entered, o_oldb, o_recs,
-      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb, o_sk, o_mref, o_msnap, o_cy;
+      o_snap, o_zl_j, o_zl_b, o_zbits, o_yb, o_sk, o_mref, o_msnap, o_cy, o_part_l2;
   // batched solver: B problems over the same X, problem b uses column b of Y
   // (ld ldy) and the rows i with rmask[i + b * ldm] != 0 (all rows if null)
   int B;
@@ -323,7 +324,7 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
 // solve problems taken from a queue, one whole path at a time; within a group
 // the CTAs split the features into slices as the single path does.
 // MINB: CTAs per SM the launch bounds promise (registers per thread <= 65536 / (256 MINB))
-template <int NGC, int CW, bool XLO, bool BATCH, int MINB>
+template <int NGC, int CW, bool XLO, bool BATCH, int MINB, bool EN = false>
 __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   constexpr int NG = CW * NGC;  // float4 granules per lane in warp-wide dots
   constexpr int CT = 32 * CW;   // chain threads (the first CW warps of CTA 0)
@@ -443,10 +444,40 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
 
   const int t_begin = (BATCH && a.lockstep) ? a.t0 : 0, t_end = (BATCH && a.lockstep) ? a.t1 : a.T;
   for (int t = t_begin; t < t_end; ++t) {
-    const double lam = __dmul_rn(vload(ctl->lambda_max), a.ratios[t]);
+    const double lam_path = __dmul_rn(vload(ctl->lambda_max), a.ratios[t]);
+    // Elastic-Net (the paper's appendix): the Lasso with L1 weight a lambda on
+    // the augmented design [X; sqrt(mu) I], [y; 0], mu = (1 - a) lambda.  The
+    // augmented rows are never formed: the augmented residual's tail is
+    // -sqrt(mu) beta, so x~_j^T rho~ = x_j^T rho - mu beta_j, ||x~_j||^2 =
+    // ||x_j||^2 + mu, ||rho~||^2 = ||rho||^2 + mu ||beta||^2.  lam is the L1
+    // weight everywhere below.
+    const double lam = EN ? __dmul_rn(a.enet_alpha, lam_path) : lam_path;
+    const double rdg = EN ? __dmul_rn(__dsub_rn(1.0, a.enet_alpha), lam_path) : 0.0;  // mu
+    const float rdgf = __double2float_rn(rdg);
+    // Elastic-Net: the extra FP32 forward error of a feature's ridge term when
+    // c~ = fl(fl(x_j^T rho) - fl(mu beta_j)) (mu and beta_j's high part each
+    // carry a relative 2^-24; the product and the difference are rounded once
+    // each), cn being the adjusted c~; and the ridge term mu beta_j in FP64
+    auto ridge_err = [&](int j, float cn) -> float {
+      const float bh = ld_beta(cx, j).x;
+      return bh != 0.f ? __fadd_ru(__fmul_ru(fabsf(__fmul_rn(rdgf, bh)), 4.8e-7f), __fmul_ru(fabsf(cn), 1.2e-7f))
+                       : 0.f;
+    };
+    auto ridge_exact = [&](int j) -> double {
+      const float2 b = ld_beta(cx, j);
+      return __dmul_rn(rdg, __dadd_rn((double)b.x, (double)b.y));
+    };
     // per-lambda table lambda / ||x_j||^2; full mask; optional restart
     for (int j = f0 + tid; j < f1; j += kThreads) {
       float4 tb = WS(float4, ftab)[j];
+      if constexpr (EN) {
+        // 1 / ||x~_j||^2 of the augmented column, for this lambda
+        const double nr = __ldcg(WS(double, nrm) + j);
+        const double den = __dadd_rn(__dmul_rn(nr, nr), rdg);
+        const df2 iv = df_from_double(den > 0.0 ? __drcp_rn(den) : 0.0);
+        tb.x = iv.h;
+        tb.y = iv.l;
+      }
       const df2 thr = df_from_double(__dmul_rn(lam, __dadd_rn((double)tb.x, (double)tb.y)));
       tb.z = thr.h;
       tb.w = thr.l;
@@ -497,19 +528,30 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           if (in) {
             c = from_gemm ? __ldcg(a.cfirst + (size_t)j + (size_t)b * a.ldc)
                           : warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-            const float E = __fmul_ru(__fmul_ru(bfc, __ldcg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
+            float E = __fmul_ru(__fmul_ru(bfc, __ldcg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
+            if constexpr (EN) {
+              const float bh = ld_beta(cx, j).x;
+              if (bh != 0.f) c = __fsub_rn(c, __fmul_rn(rdgf, bh));  // x~_j^T rho~
+              E = __fadd_ru(E, ridge_err(j, c));
+            }
             mlo = fmaxf(mlo, __fsub_rd(fabsf(c), E));
           }
           if (lane == 0) WS(float, ctil)[j] = c;
         }
         if (lane == 0) atomicMax(&ctl->mlo_bits, __float_as_uint(fmaxf(mlo, 0.f)));
-        double l1p = 0.0;
+        double l1p = 0.0, l2p = 0.0;
         for (int j = f0 + tid; j < f1; j += kThreads) {
           const float2 b = ld_beta(cx, j);
-          l1p = __dadd_rn(l1p, fabs(__dadd_rn((double)b.x, (double)b.y)));
+          const double bv = __dadd_rn((double)b.x, (double)b.y);
+          l1p = __dadd_rn(l1p, fabs(bv));
+          if constexpr (EN) l2p = __fma_rn(bv, bv, l2p);
         }
         l1p = block_sum_d(l1p, dbuf);
         if (tid == 0) WS(double, part_l1)[cta] = l1p;
+        if constexpr (EN) {
+          l2p = block_sum_d(l2p, dbuf);
+          if (tid == 0) WS(double, part_l2)[cta] = l2p;
+        }
       }
       GSYNC();
       // (C2) exact refinement of the candidates for the maximum
@@ -520,10 +562,13 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           if (!in) continue;
           const float c = __ldcg(WS(float, ctil) + j);
           const float nf = __ldcg(WS(float, nrmf) + j);
-          const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+          float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+          if constexpr (EN) E = __fadd_ru(E, ridge_err(j, c));
           if (__fadd_ru(fabsf(c), E) >= mlo) {
             const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l), __fmul_ru(nf, rnormf));
-            const double cv = fabs(df_to_double(ce));
+            double cv = df_to_double(ce);
+            if constexpr (EN) cv = __dsub_rn(cv, ridge_exact(j));
+            cv = fabs(cv);
             if (lane == 0) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(cv));
           }
         }
@@ -533,6 +578,13 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
       double l1 = 0.0;
       for (int c = tid; c < G; c += kThreads) l1 = __dadd_rn(l1, __ldcg(WS(double, part_l1) + c));
       l1 = block_sum_d(l1, dbuf);
+      double l2 = 0.0;
+      if constexpr (EN) {
+        // ||rho~||^2 = ||rho||^2 + mu ||beta||^2
+        for (int c = tid; c < G; c += kThreads) l2 = __dadd_rn(l2, __ldcg(WS(double, part_l2) + c));
+        l2 = block_sum_d(l2, dbuf);
+        rr = __dadd_rn(rr, __dmul_rn(rdg, l2));
+      }
       const double m = __longlong_as_double((long long)vload(ctl->m_bits));
       double alpha;
       if (a.dual_point == 0) {
@@ -555,11 +607,16 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
         d2 = __fma_rn(dd, dd, d2);
       }
       d2 = block_sum_d(d2, dbuf);
+      if constexpr (EN) {
+        // the augmented rows: (lambda alpha (-sqrt(mu) beta_j))^2
+        const double la = __dmul_rn(lam, alpha);
+        d2 = __dadd_rn(d2, __dmul_rn(__dmul_rn(la, la), __dmul_rn(rdg, l2)));
+      }
       const double yy = vload(ctl->yy);
       const double P = __dadd_rn(__dmul_rn(0.5, rr), __dmul_rn(lam, l1));
       const double D = __dsub_rn(__dmul_rn(0.5, yy), __dmul_rn(0.5, d2));
       const double Gap = __dsub_rn(P, D);
-      const double tau = 2.0 * (double)(a.n + a.p + 8) * u64 * (rr + lam * l1 + yy + d2);
+      const double tau = 2.0 * (double)(a.n + a.p + (EN ? a.p : 0) + 8) * u64 * (rr + lam * l1 + yy + d2);
       const double Gs = (Gap > 0.0 ? Gap : 0.0) + tau;
       double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
       if (a.refined_radius == 1) {
@@ -605,10 +662,16 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           if (was) {
             const float c = __ldcg(WS(float, ctil) + j);
             const float nf = __ldcg(WS(float, nrmf) + j);
-            const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+            float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+            float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
+            float nfr = nf;  // ||x~_j|| rounded up: the radius term's norm
+            if constexpr (EN) {
+              E = __fadd_ru(E, ridge_err(j, c));
+              nfr = __fsqrt_ru(__fadd_ru(__fmul_ru(nf, nf), __double2float_ru(rdg)));
+              nfl = __fsqrt_rd(__fadd_rd(__fmul_rd(nfl, nfl), __double2float_rd(rdg)));
+            }
             // rigorous FP32 brackets of mu_j = |c_j| |alpha| + r ||x_j||
-            const float mu_hi = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(c), E), aaf_hi), __fmul_ru(radf_hi, nf));
-            const float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
+            const float mu_hi = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(c), E), aaf_hi), __fmul_ru(radf_hi, nfr));
             const float clo = fmaxf(__fsub_rd(fabsf(c), E), 0.f);
             const float mu_lo = __fadd_rd(__fmul_rd(clo, aaf_lo), __fmul_rd(radf_lo, nfl));
             // a feature the sphere screens for certain is screened by the
@@ -626,7 +689,11 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
             ambm &= ambm - 1;
             const int jj = w0 + l;
             const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldcg(WS(float, nrmf) + jj), rnormf));
-            const double cj = df_to_double(ce), xn = __ldcg(WS(double, nrm) + jj);
+            double cj = df_to_double(ce), xn = __ldcg(WS(double, nrm) + jj);
+            if constexpr (EN) {
+              cj = __dsub_rn(cj, ridge_exact(jj));
+              xn = __dsqrt_rn(__dadd_rn(__dmul_rn(xn, xn), rdg));
+            }
             const double mu = __dadd_rn(__dmul_rn(fabs(cj), aa), __dmul_rn(rad, xn));
             bool kp = !(mu < 1.0);
             if (dome) {
@@ -709,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
             mout[(long long)t * a.words + w] = __ldcg(WS(uint32_t, mask) + w);
         if (cta == 0 && tid == 0) {
           lasso_path_stats st;
-          st.lambda = lam;
+          st.lambda = lam_path;
           st.primal = P;
           st.dual = D;
           st.gap = Gap;
@@ -880,7 +947,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               for (int c = tid; c < nc; c += kThreads)
                 WS(int, chain)[c] = (forced >= 0) ? (c == 0 ? forced : __ldcg(sup + si + c - 1)) : __ldcg(sup + si + c);
               __syncthreads();
-              const float rb = rho_bound_from_regs<NGC>(cx, rh, lam, nc, fbuf);
+              const float rb = rho_bound_from_regs<NGC, EN>(cx, rh, lam, nc, fbuf, rdg);
               if (tid == 0) {
                 ctl->rho_bound = rb;
                 ctl->nc = nc;
@@ -890,7 +957,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               }
               store_rho_regs<NGC, CW>(cx, WS(float, snap), WS(float, snap) + a.ldw, rh, rl);  // snapshot 0
               __syncthreads();
-              run_chain<NGC, CW, XLO>(cx, cs, ring, jl, nc, rb, rh, rl, rbits);
+              run_chain<NGC, CW, XLO, EN>(cx, cs, ring, jl, nc, rb, rh, rl, rbits, df_from_double(rdg));
               __threadfence();
               if (prof_thread) ctl->prof[5] += (unsigned long long)nc;
             }
@@ -1231,9 +1298,10 @@ __global__ void rho_init_kernel(const XT* X, long long ldx, int n, int p, const 
 
 // lambda_max = ||X^T y||_inf must be > 0 (otherwise every lambda_t is 0) and
 // every ratio must lie in (0, 1]; violations are reported as INVALID_ARG.
-__global__ void finish_setup_kernel(Ctrl* ctl, const double* ratios, int T) {
+// For the Elastic-Net with mixing a, beta = 0 is optimal from ||X^T y||_inf / a.
+__global__ void finish_setup_kernel(Ctrl* ctl, const double* ratios, int T, double enet_alpha) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    ctl->lambda_max = __longlong_as_double((long long)ctl->m_bits);
+    ctl->lambda_max = __ddiv_rn(__longlong_as_double((long long)ctl->m_bits), enet_alpha);
     ctl->m_bits = 0ull;
     ctl->mlo_bits = 0u;
     bool bad = !(ctl->lambda_max > 0.0);
@@ -1328,7 +1396,7 @@ struct Layout {
 enum {
   L_ctrl, L_cnt, L_part_l1, L_nrm, L_nrmf, L_ftab, L_bdf, L_b0df, L_rho_h, L_rho_l, L_rho0_h, L_rho0_l, L_ctil,
   L_mask, L_A, L_sup0, L_sup1, L_chain, L_entered, L_oldb, L_recs, L_snap, L_zl_j, L_zl_b, L_zbits, L_yb, L_sk,
-  L_mref, L_msnap, L_cy, L_N
+  L_mref, L_msnap, L_cy, L_part_l2, L_N
 };
 
 Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
@@ -1371,6 +1439,7 @@ Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes) {
   take(L_mref, sizeof(float) * p);
   take(L_msnap, sizeof(float) * (s_cap + 2));
   take(L_cy, sizeof(double) * p);
+  take(L_part_l2, sizeof(double) * kMaxGrid);
   L.region = off;
   L.planes = planes ? 2 * align256(sizeof(float) * (size_t)ldw * (size_t)p) : 0;
   L.total = L.region + L.planes;
@@ -1413,13 +1482,14 @@ void set_offsets(Args& a, const Layout& L) {
   a.o_mref = L.o[L_mref];
   a.o_msnap = L.o[L_msnap];
   a.o_cy = L.o[L_cy];
+  a.o_part_l2 = L.o[L_part_l2];
   a.ldw = L.ldw;
   a.s_cap = L.s_cap;
 }
 
-template <int NGC, int CW, bool XLO, bool BATCH, int MINB = 1>
+template <int NGC, int CW, bool XLO, bool BATCH, int MINB = 1, bool EN = false>
 const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&path_kernel<NGC, CW, XLO, BATCH, MINB>);
+  return reinterpret_cast<const void*>(&path_kernel<NGC, CW, XLO, BATCH, MINB, EN>);
 }
 
 // Chain shape for n rows.  A coordinate step is one warp's dependent
@@ -1450,6 +1520,13 @@ const void* pick_kernel(ChainShape c, bool xlo, bool batch, int per_sm = 1) {
          : c.ngc == 2 ? kernel_ptr<2, 4, false, false>() : kernel_ptr<4, 4, false, false>();
 }
 
+// the single path on an FP32 design with the Elastic-Net's ridge term
+const void* pick_kernel_enet(ChainShape c) {
+  if (c.cw == 1) return kernel_ptr<1, 1, false, false, 1, true>();
+  return c.ngc == 1 ? kernel_ptr<1, 4, false, false, 1, true>()
+         : c.ngc == 2 ? kernel_ptr<2, 4, false, false, 1, true>() : kernel_ptr<4, 4, false, false, 1, true>();
+}
+
 void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) {
   a.n = (int)n;
   a.p = (int)p;
@@ -1460,6 +1537,7 @@ void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) 
   a.dual_point = o.dual_point;
   a.screen_rule = o.screen_rule;
   a.refined_radius = o.refined_radius;
+  a.enet_alpha = o.enet_alpha;
   a.xtr_scope = o.xtr_scope;
   a.warm_start = o.warm_start;
   a.max_epochs = o.max_epochs;
@@ -1535,7 +1613,9 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
   }
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + a.o_ctrl);
   const ChainShape cs = chain_shape(n, false);
-  const void* kfn = pick_kernel(cs, f64, false);
+  const bool enet = o.enet_alpha < 1.0;
+  if (enet && f64) return set_error(LASSO_ERR_INVALID_ARG, "enet_alpha < 1 needs an FP32 design");
+  const void* kfn = enet ? pick_kernel_enet(cs) : pick_kernel(cs, f64, false);
   DevInfo d{};
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
@@ -1580,7 +1660,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
     rho_init_kernel<float><<<rb, 256, 0, stream>>>(static_cast<const float*>(X), ldx, (int)n, (int)p, y, beta0,
                                                    rho_h, rho_l, rho0_h, rho0_l, (int)a.ldw, o.gap_tol_rel, ctrl);
   CUDA_TRY(cudaGetLastError());
-  finish_setup_kernel<<<1, 32, 0, stream>>>(ctrl, ratios, T);
+  finish_setup_kernel<<<1, 32, 0, stream>>>(ctrl, ratios, T, o.enet_alpha);
   CUDA_TRY(cudaGetLastError());
   void* params[] = {&a};
   CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), params, dyn, stream));

@@ -47,7 +47,8 @@ class LassoOpts(ctypes.Structure):
                 ("max_epochs", ctypes.c_int64), ("gap_tol_rel", ctypes.c_double),
                 ("gemm_dtype", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
                 ("gemm_tile_n", ctypes.c_int32), ("batch_group", ctypes.c_int32),
-                ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32)]
+                ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32),
+                ("enet_alpha", ctypes.c_double)]
 
 
 class LassoPathStats(ctypes.Structure):

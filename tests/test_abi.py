@@ -46,6 +46,7 @@ def test_default_opts(pkg):
     assert (o.screen_period, o.dual_point, o.xtr_scope, o.warm_start) == (10, 0, 0, 1)
     assert o.max_epochs == 100000 and o.gap_tol_rel == 1e-6 and o.gemm_dtype == pkg.LASSO_BF16
     assert (o.batch_ctas_per_sm, o.gemm_tile_n, o.batch_group, o.screen_rule, o.refined_radius) == (0, 0, 0, 0, 0)
+    assert o.enet_alpha == 1.0
 
 
 def test_lambda_grid_matches_oracle(pkg):
@@ -97,7 +98,8 @@ def test_argument_errors(pkg, kw, status):
                                          ("warm_start", 3), ("max_epochs", -1), ("gap_tol_rel", -1.0),
                                          ("gemm_dtype", 7), ("batch_ctas_per_sm", 3), ("gemm_tile_n", 96),
                                          ("batch_group", 65), ("batch_group", -1), ("screen_rule", 2),
-                                         ("refined_radius", 2)])
+                                         ("refined_radius", 2), ("enet_alpha", 0.0), ("enet_alpha", 1.5),
+                                         ("enet_alpha", float("nan"))])
 def test_option_errors(pkg, field, value):
     o = pkg.lasso_default_opts(**{field: value})
     with pytest.raises(pkg.LassoError) as e:
@@ -158,5 +160,22 @@ def test_batch_group_needs_fp32_checks(pkg):
     o = pkg.lasso_default_opts(batch_group=4)  # default gemm_dtype is LASSO_BF16
     with pytest.raises(pkg.LassoError) as e:
         pkg.lasso_batch(1 << 12, 10, 20, 12, 1 << 12, 10, None, 0, 2, 1 << 12, 3, None, 0, o, 1 << 12, None,
+                        1 << 12, 1 << 12, 1 << 20, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+
+
+def test_enet_restrictions(pkg):
+    """The Elastic-Net runs on the single path with an FP32 design and the
+    sphere test; the host rejects the rest before any CUDA call."""
+    o = pkg.lasso_default_opts(enet_alpha=0.5)
+    with pytest.raises(pkg.LassoError) as e:
+        _call(pkg, opts=o, x_dtype=pkg.LASSO_F64)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError) as e:
+        _call(pkg, opts=pkg.lasso_default_opts(enet_alpha=0.5, screen_rule=1))
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    with pytest.raises(pkg.LassoError) as e:
+        pkg.lasso_batch(1 << 12, 10, 20, 12, 1 << 12, 10, None, 0, 2, 1 << 12, 3, None, 0,
+                        pkg.lasso_default_opts(enet_alpha=0.5, gemm_dtype=pkg.LASSO_F32), 1 << 12, None,
                         1 << 12, 1 << 12, 1 << 20, None)
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG

@@ -146,6 +146,37 @@ def test_refined_radius_parity(pkg, opt):
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("seed,n,p,a,opt", [
+    (131, 77, 1537, 0.5, {}),       # one-warp chain
+    (132, 500, 1200, 0.8, {}),      # four chain warps, one granule per lane
+    (133, 611, 900, 0.3, {}),       # two granules per lane
+    (134, 1100, 1300, 0.6, {}),     # four granules per lane
+    (135, 90, 1200, 0.5, dict(dual_point=1, xtr_scope=1, refined_radius=1)),
+])
+def test_enet_parity(pkg, seed, n, p, a, opt):
+    """Elastic-Net (enet_alpha = a, the paper's appendix): the GPU keeps the
+    augmented rows implicit, the oracle builds [X; sqrt((1 - a) lambda) I] at
+    every lambda; masks, supports, pass and check counts, objectives and
+    coefficients agree."""
+    prob = gen.small_problem(seed, n, p, dtype=np.float32, k=max(2, min(n, p) // 20), noise=0.2, correlated=True)
+    ratios = oracle.lambda_ratios(12, 2.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-9, enet_alpha=a, **opt)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-9, enet_alpha=a, **opt)
+    assert_parity(g, o)
+
+
+def test_enet_from_a_starting_point(pkg):
+    """The Elastic-Net from an outside beta0 with warm starts off (every
+    lambda restarts from it; the grid starts below lambda_max)."""
+    prob = gen.small_problem(136, 80, 900, dtype=np.float32, k=4, noise=0.2)
+    rng = np.random.default_rng(136)
+    beta0 = 0.5 * rng.standard_normal(900) * (rng.random(900) < 0.03)
+    ratios = oracle.lambda_ratios(8, 1.5)[1:]
+    g = run_gpu(pkg, prob, ratios, beta0=beta0, warm_start=0, gap_tol_rel=1e-9, enet_alpha=0.4)
+    o = run_orc(prob, ratios, beta0=beta0, warm_start=0, gap_tol_rel=1e-9, enet_alpha=0.4)
+    assert_parity(g, o)
+
+
 def test_beta0_and_screened_nonzero(pkg):
     """A warm start with nonzero coefficients on inactive features exercises
     the removal of screened nonzero coefficients (Remark 3)."""
