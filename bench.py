@@ -63,6 +63,8 @@ def _args():
                     help="problems of the batched workload timed one at a time on the plain path")
     ap.add_argument("--screen-rule", type=int, choices=[0, 1], default=0,
                     help="0: GAP SAFE sphere (default); 1: sphere and GAP SAFE dome")
+    ap.add_argument("--enet-alpha", type=float, default=1.0,
+                    help="Elastic-Net mixing a in (0, 1]; 1 (default) is the Lasso")
     return ap.parse_args()
 
 
@@ -88,9 +90,9 @@ def aggregate_ranks(total_ms, solves, device=None):
     return float(t.item()), int(round(float(s.item())))
 
 
-def _workload(screen_rule=0):
+def _workload(screen_rule=0, enet_alpha=1.0):
     import gen
-    return dict(gen.workload2(), screen_rule=screen_rule)
+    return dict(gen.workload2(), screen_rule=screen_rule, enet_alpha=enet_alpha)
 
 
 def _config(w):
@@ -99,6 +101,7 @@ def _config(w):
                         f"check every {w['f']} passes, gap<=1e-6*||y||^2",
             "n": w["n"], "p": w["p"], "T": w["T"], "screen_period": w["f"], "gap_tol_rel": w["tol"],
             "screen_rule": "dome" if w.get("screen_rule", 0) == 1 else "sphere",
+            "enet_alpha": w.get("enet_alpha", 1.0),
             "l2": "flushed (512 MiB write) before every timed step",
             "parallelism": "replicas (one independent path per GPU)"}
 
@@ -110,12 +113,18 @@ def _oracle_sample(w, T=CPU_SAMPLE_T):
     ratios = oracle.lambda_ratios(w["T"], w["delta"])[:T]
     t0 = time.perf_counter()
     out = oracle.lasso_path(w["XT"], w["y"], ratios, n=w["n"], screen_period=w["f"], gap_tol_rel=w["tol"],
-                            screen_rule=w.get("screen_rule", 0))
+                            screen_rule=w.get("screen_rule", 0), enet_alpha=w.get("enet_alpha", 1.0))
     dt = time.perf_counter() - t0
     return int((out["stats"]["converged"] == 1).sum()), dt
 
 
+ENET_ORACLE_NOTE = ("the oracle's Elastic-Net builds the (n+p) x p augmented design at every lambda: "
+                    "20 GB at 500 x 50000, so it is not timed at this size")
+
+
 def _cpu_baseline(w):
+    if w.get("enet_alpha", 1.0) < 1.0:
+        return {"unavailable": ENET_ORACLE_NOTE}
     solves, dt = _oracle_sample(w)
     return {"value": solves / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle (plain C, single thread) on the first {CPU_SAMPLE_T} of the {w['T']} lambdas "
@@ -201,7 +210,10 @@ def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    w = _workload(args.screen_rule)
+    w = _workload(args.screen_rule, args.enet_alpha)
+    if args.enet_alpha < 1.0:
+        print(json.dumps({"impl": "reference", "unavailable": ENET_ORACLE_NOTE}), flush=True)
+        return
     for _ in range(args.warmup):
         _oracle_sample(w)
     total_s, total_solves, times = 0.0, 0, []
@@ -238,7 +250,7 @@ def run_ours(args):
     build()
     import paper_1505_03410_gb300 as pkg
 
-    w = _workload(args.screen_rule)
+    w = _workload(args.screen_rule, args.enet_alpha)
     n, p, T = w["n"], w["p"], w["T"]
     ratios_h = pkg.lasso_lambda_grid(T, w["delta"])
     if 0 < args.lambdas < T:
@@ -248,7 +260,8 @@ def run_ours(args):
     XT = torch.from_numpy(w["XT"]).to(dev)
     y = torch.from_numpy(w["y"]).to(dev)
     ratios = torch.from_numpy(ratios_h).to(dev)
-    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=args.screen_rule)
+    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=args.screen_rule,
+                                  enet_alpha=args.enet_alpha)
     words = (p + 31) // 32
     beta_out = torch.empty((T, p), dtype=torch.float64, device=dev)
     mask_out = torch.empty((T, words), dtype=torch.int32, device=dev)
