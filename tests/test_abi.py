@@ -179,3 +179,30 @@ def test_enet_restrictions(pkg):
                         pkg.lasso_default_opts(enet_alpha=0.5, gemm_dtype=pkg.LASSO_F32), 1 << 12, None,
                         1 << 12, 1 << 12, 1 << 20, None)
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_the_header(pkg, tmp_path):
+    """The ctypes mirrors of lasso_opts and lasso_path_stats have the field
+    offsets and sizes a C compiler gives the declarations in lassogs.h."""
+    import ctypes
+    import os
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    mirrors = {"lasso_opts": pkg.LassoOpts, "lasso_path_stats": pkg.LassoPathStats}
+    lines = ['#include <stdio.h>', '#include "lassogs.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            cf = "lambda" if fname == "lambda_" else fname
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", inc, "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
