@@ -42,6 +42,9 @@
  *       unchanged, so the certified gap belongs to the returned beta.
  *   R9  lambda_t = lambda_max * 10^(-delta t / (T-1)), t = 0..T-1 (Sec. 3.3),
  *       passed in as the ratios lambda_t / lambda_max.
+ *   (R10-R13 concern the batched problems on row subsets, outside starting
+ *   points at lambda_max and the learned start; orc_lasso_batch and
+ *   oracle/lista.py state what they need of them.)
  *   R14 GAP SAFE dome (screen_rule == 1, Eq. (11) with the parameters of the
  *       appendix): ball center (y/lambda + theta)/2, ball radius R/2 with
  *       R = ||y/lambda - theta||, unit normal (y/lambda - theta)/R and ratio
