@@ -12,7 +12,10 @@ Pins (checked by the ``not gpu`` tests): beta = 0 for lambda >= lambda_max
 (Sec. 1.2), soft-thresholding closed form on orthonormal designs, brute-force
 support enumeration for p <= 12 (``oracle.bruteforce``), KKT conditions
 (Eq. (4)), safety of every sphere (Thm. 2 + Prop. 1), the sequential identity
-of Prop. 3, finite identification (Thm. 1).
+of Prop. 3, finite identification (Thm. 1); for the options: the dome's
+support function and parameters against sampled maxima over the sets they come
+from (Eq. (11)), Thm. 2's refined radius recomputed from its definition, and
+the Elastic-Net's closed form, KKT conditions and exact solution (appendix).
 """
 from __future__ import annotations
 
