@@ -206,3 +206,44 @@ def test_struct_layouts_match_the_header(pkg, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "lassogs.h"
+
+int main(void) {
+  lasso_opts o;
+  lasso_default_opts(&o);
+  double r[5];
+  if (lasso_lambda_grid(5, 2.0, r) != LASSO_OK) return 1;
+  printf("grid %.17g %.17g\n", r[0], r[4]);
+  printf("ws %zu\n", lasso_path_workspace_size(500, 50000, LASSO_F32, &o));
+  /* a host-side argument error: no device work, a message, INVALID_ARG */
+  lasso_status st = lasso_path(NULL, LASSO_F32, 8, 16, 8, NULL, NULL, 4, NULL, &o, NULL, NULL, NULL, NULL, 0, NULL);
+  printf("status %d %s\n", (int)st, strlen(lasso_last_error()) > 0 ? "message" : "none");
+  o.screen_period = 0;
+  printf("bad %zu\n", lasso_path_workspace_size(10, 10, LASSO_F32, &o));
+  return 0;
+}
+"""
+
+
+def test_c_client_links_and_calls_the_host_api(pkg, tmp_path):
+    """A plain C program compiles against include/lassogs.h, links
+    liblassogs.so and calls its host-only entry points: the ABI needs neither
+    Python nor C++ on the caller's side."""
+    import subprocess
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(pkg.lassogs.LIB_PATH)
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src),
+                           "-L", libdir, "-llassogs", f"-Wl,-rpath,{libdir}"])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    grid = out[0].split()
+    assert float(grid[1]) == 1.0 and float(grid[2]) == pkg.lasso_lambda_grid(5, 2.0)[4]
+    assert int(out[1].split()[1]) == pkg.lasso_path_workspace_size(500, 50000, pkg.LASSO_F32)
+    assert out[2] == f"status {pkg.LASSO_ERR_INVALID_ARG} message"
+    assert out[3] == "bad 0"
