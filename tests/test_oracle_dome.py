@@ -61,7 +61,8 @@ def _states(orc, X, y, lam, passes):
     return out
 
 
-def test_dome_value_is_the_maximum_over_the_safe_set(orc):
+@pytest.mark.parametrize("dual_point", [0, 1])
+def test_dome_value_is_the_maximum_over_the_safe_set(orc, dual_point):
     """For three rows the set S = {z : (z - y/l)^T (z - theta) <= 0,
     ||z - y/l|| >= r(beta)} is sampled on its boundary (the part of the sphere
     with diameter [theta, y/l] outside the ball B(y/l, r), and the circle
@@ -79,7 +80,7 @@ def test_dome_value_is_the_maximum_over_the_safe_set(orc):
     w0 = _unit_sphere(rng, 20000, n)
     checked = 0
     for beta, rho in _states(orc, X, y, lam, (1, 3)):
-        res = orc.check(X, y, beta, rho, lam, screen_rule=1)
+        res = orc.check(X, y, beta, rho, lam, screen_rule=1, dual_point=dual_point)
         theta = res["alpha"] * rho
         yl = y / lam
         R = np.linalg.norm(yl - theta)

@@ -118,3 +118,43 @@ def test_enet_alpha_one_is_the_lasso(orc):
     b = orc.lasso_path(X, y, ratios, gap_tol_rel=1e-10, enet_alpha=1.0)
     np.testing.assert_array_equal(a["beta"], b["beta"])
     np.testing.assert_array_equal(a["mask"], b["mask"])
+
+
+def test_enet_with_the_dome_is_safe(orc):
+    """The dome test on the augmented design (Eq. (11) applied to the
+    Elastic-Net's Lasso form): every feature it screens is zero at the exact
+    Elastic-Net optimum, and the tight path equals the enumeration's."""
+    a = 0.5
+    prob = gen.small_problem(37, 14, 10, dtype=np.float64, k=3, noise=0.3)
+    X, y = _dense(prob), prob["y"]
+    ratios = orc.lambda_ratios(6, 1.5)
+    out = orc.lasso_path(X, y, ratios, gap_tol_rel=1e-15, max_epochs=200000, enet_alpha=a, screen_rule=1,
+                         screen_period=1)
+    lmax = out["lambda_max"]
+    screened = 0
+    for t in range(1, len(ratios)):
+        lam = lmax * ratios[t]
+        Xa = np.vstack([X, np.sqrt((1 - a) * lam) * np.eye(10)])
+        bb, _ = lasso_bruteforce(Xa, np.concatenate([y, np.zeros(10)]), a * lam)
+        kept = orc.unpack_mask(out["mask"][t], 10)
+        assert np.all(bb[~kept] == 0)
+        screened += int((~kept).sum())
+        np.testing.assert_allclose(out["beta"][t], bb, atol=1e-6)
+    assert screened > 0
+
+
+def test_enet_batch_equals_independent_paths(orc):
+    """Row-subset Elastic-Net problems: each batched solve equals the plain
+    Elastic-Net path on the gathered rows."""
+    prob = gen.small_problem(38, 30, 40, dtype=np.float64, k=3)
+    X, y = _dense(prob), prob["y"]
+    rng = np.random.default_rng(38)
+    B = 3
+    rm = (rng.random((B, 30)) < 0.7).astype(np.uint8)
+    Y = np.stack([y * rm[b] for b in range(B)])
+    ratios = orc.lambda_ratios(5, 1.5)
+    out = orc.lasso_batch(X, Y, ratios, row_mask=rm, gap_tol_rel=1e-10, enet_alpha=0.6)
+    for b in range(B):
+        rows = rm[b] != 0
+        ref = orc.lasso_path(X[rows], y[rows], ratios, gap_tol_rel=1e-10, enet_alpha=0.6)
+        np.testing.assert_array_equal(out["beta"][b], ref["beta"])

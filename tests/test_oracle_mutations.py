@@ -83,7 +83,7 @@ PIN_CALLS = [
     (pins.test_dual_point_eq8_is_projection_on_span, {}),
     (pins.test_refined_radius_of_thm2, {}),
     (dome.test_dome_support_matches_sampled_maximum, {"alpha": 0.35}),
-    (dome.test_dome_value_is_the_maximum_over_the_safe_set, {}),
+    (dome.test_dome_value_is_the_maximum_over_the_safe_set, {"dual_point": 0}),
     (dome.test_dome_lies_inside_the_sphere, {}),
     (dome.test_every_dome_contains_dual_optimum, {}),
     (dome.test_dome_path_reaches_the_exact_solution, {"seed": 44, "n": 20, "p": 8}),
