@@ -158,3 +158,22 @@ def test_enet_batch_equals_independent_paths(orc):
         rows = rm[b] != 0
         ref = orc.lasso_path(X[rows], y[rows], ratios, gap_tol_rel=1e-10, enet_alpha=0.6)
         np.testing.assert_array_equal(out["beta"][b], ref["beta"])
+
+
+def test_enet_hand_examples(orc):
+    """Hand-derived Elastic-Net cases (tests/golden/hand_examples.json):
+    coefficients, primal and dual values at lambda, with lambda_max =
+    ||X^T y||_inf / a."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
+    for case in json.load(open(path))["enet_cases"]:
+        X = np.array(case["X"], dtype=np.float64)
+        y = np.array(case["y"], dtype=np.float64)
+        a = case["a"]
+        ratio = case["lambda"] / (np.abs(X.T @ y).max() / a)
+        out = orc.lasso_path(X, y, [1.0, ratio], gap_tol_rel=1e-15, enet_alpha=a)
+        assert out["stats"]["lambda"][1] == pytest.approx(case["lambda"], rel=1e-15)
+        np.testing.assert_allclose(out["beta"][1], case["beta"], atol=1e-12)
+        assert out["stats"]["primal"][1] == pytest.approx(case["primal"], rel=1e-12)
+        assert out["stats"]["dual"][1] == pytest.approx(case["dual"], rel=1e-12)
