@@ -91,6 +91,7 @@ PIN_CALLS = [
     (enet.test_enet_first_feature_enters, {}),
     (enet.test_enet_bruteforce_agreement, {"seed": 32, "n": 20, "p": 8, "a": 0.5}),
     (enet.test_enet_kkt_at_tight_solution, {}),
+    (enet.test_enet_hand_examples, {}),
 ]
 
 
