@@ -25,6 +25,11 @@
 //                       after it starts with that coordinate.
 //   A zero coefficient that stays zero leaves rho unchanged, so the iterates
 //   are those of plain cyclic coordinate descent over the safe-active set.
+//
+// Options of the check: the GAP SAFE dome of Eq. (11) beside the sphere, and
+// the sphere radius of Thm. 2.  Instantiations with EN = true solve the
+// Elastic-Net of the paper's appendix as the Lasso on the augmented design
+// [X; sqrt(mu) I], whose extra rows stay implicit.
 #include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
