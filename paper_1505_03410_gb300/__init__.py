@@ -13,5 +13,6 @@ from .lassogs import (EXPORTED, LASSO_BF16, LASSO_ERR_CUDA, LASSO_ERR_INVALID_AR
                       lasso_batch_workspace_size, solve_batch, lasso_correlations_bf16,
                       lasso_correlations_f32, lasso_batch_tune, lasso_batch_tune_candidates,
                       lasso_batch_tune_workspace_size, tune_batch)
+from .shard import problem_range, solve_batch_sharded  # noqa: F401  (one process per GPU)
 from . import lista  # noqa: F401  (learned warm start, include/lista.h)
 from .lista import ListaNet  # noqa: F401
