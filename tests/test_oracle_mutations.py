@@ -44,6 +44,7 @@ MUTANTS = [
     ("Eq. (8) clipped to the wrong side", "if (a < -lim) a = -lim;", "if (a < -lim) a = lim;"),
     ("lambda_max from the smallest correlation", "if (fabs(c0[j]) > lmax) { lmax = fabs(c0[j]); arg = j; }",
      "if (j == 0 || fabs(c0[j]) < lmax) { lmax = fabs(c0[j]); arg = j; }"),
+    ("gap rounding bound dropped", "double tau = 2.0 * (double)(n + p + 8) * u", "double tau = 0.0 * (double)(n + p + 8) * u"),
     # the dome test (Eq. (11), appendix)
     ("dome normal with the main text's sign", "double nx = (xy - xt) / dR;", "double nx = (xt - xy) / dR;"),
     ("dome ratio with the opposite sign", "dal = 2.0 * q - 1.0;", "dal = 1.0 - 2.0 * q;"),
@@ -82,6 +83,7 @@ PIN_CALLS = [
     (pins.test_prop3_sequential_identity, {}),
     (pins.test_dual_point_eq8_is_projection_on_span, {}),
     (pins.test_refined_radius_of_thm2, {}),
+    (pins.test_gap_rounding_bound_holds, {}),
     (dome.test_dome_support_matches_sampled_maximum, {"alpha": 0.35}),
     (dome.test_dome_value_is_the_maximum_over_the_safe_set, {"dual_point": 0}),
     (dome.test_dome_lies_inside_the_sphere, {}),

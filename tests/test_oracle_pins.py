@@ -381,3 +381,32 @@ def test_screening_a_nonzero_coefficient(orc):
     assert not orc.unpack_mask(out["mask"][0], 10)[k]
     np.testing.assert_allclose(out["beta"][0], bb, atol=1e-9)
     assert out["stats"]["primal"][0] == pytest.approx(Pb, rel=1e-12)
+
+
+def test_gap_rounding_bound_holds(orc):
+    """R7: the FP64 gap the check computes differs from the exact gap of the
+    same (beta, rho, alpha) -- evaluated in rational arithmetic -- by at most
+    the inflation tau the radius adds.  The cases include a nearly converged
+    iterate, where the gap is far below its terms."""
+    from fractions import Fraction as F
+    prob = _problem(22, 20, 12, k=3, noise=0.2)
+    X, y = _dense(prob), prob["y"]
+    lmax = np.abs(X.T @ y).max()
+    checked = 0
+    for ratio in (0.6, 0.2):
+        lam = ratio * lmax
+        tight = orc.lasso_path(X, y, [1.0, ratio], gap_tol_rel=1e-15)["beta"][1]
+        beta0 = np.zeros(12)
+        for beta in (beta0, 0.5 * tight, tight):
+            rho = y - X @ beta
+            res = orc.check(X, y, beta, rho, lam)
+            a = F(res["alpha"])
+            L = F(lam)
+            rr = sum(F(v) * F(v) for v in rho)
+            l1 = sum(abs(F(v)) for v in beta)
+            d2 = sum((L * (a * F(r)) - F(v)) ** 2 for r, v in zip(rho, y))
+            yy = sum(F(v) * F(v) for v in y)
+            G = (rr / 2 + L * l1) - (yy / 2 - d2 / 2)
+            assert abs(F(res["gap"]) - G) <= F(res["tau"]), (float(G), res["gap"], res["tau"])
+            checked += 1
+    assert checked == 6
