@@ -177,3 +177,34 @@ def test_enet_hand_examples(orc):
         np.testing.assert_allclose(out["beta"][1], case["beta"], atol=1e-12)
         assert out["stats"]["primal"][1] == pytest.approx(case["primal"], rel=1e-12)
         assert out["stats"]["dual"][1] == pytest.approx(case["dual"], rel=1e-12)
+
+
+COMBOS = [
+    dict(), dict(dual_point=1), dict(xtr_scope=1), dict(screen_rule=1), dict(refined_radius=1),
+    dict(warm_start=False), dict(dual_point=1, xtr_scope=1, screen_rule=1, refined_radius=1),
+    dict(enet_alpha=0.7), dict(enet_alpha=0.7, dual_point=1, xtr_scope=1),
+    dict(enet_alpha=0.4, screen_rule=1, refined_radius=1), dict(enet_alpha=0.4, warm_start=False, screen_period=1),
+]
+
+
+@pytest.mark.parametrize("opt", COMBOS, ids=[",".join(f"{k}={v}" for k, v in c.items()) or "default" for c in COMBOS])
+def test_every_option_combination_reaches_the_exact_solution(orc, opt):
+    """Whatever the dual point, scope, safe region, radius, warm start and
+    mixing, the screened path ends at the exact optimum (support enumeration
+    on the augmented design; a = 1 is the Lasso) and screens only features
+    that are zero there."""
+    a = opt.get("enet_alpha", 1.0)
+    prob = gen.small_problem(39, 16, 10, dtype=np.float64, k=3, noise=0.3, correlated=True)
+    X, y = _dense(prob), prob["y"]
+    ratios = orc.lambda_ratios(6, 1.5)
+    out = orc.lasso_path(X, y, ratios, gap_tol_rel=1e-15, max_epochs=200000, **opt)
+    assert out["status"] == 0
+    lmax = out["lambda_max"]
+    for t in range(1, len(ratios)):
+        lam = lmax * ratios[t]
+        Xa = np.vstack([X, np.sqrt((1 - a) * lam) * np.eye(10)])
+        bb, _ = lasso_bruteforce(Xa, np.concatenate([y, np.zeros(10)]), a * lam)
+        kept = orc.unpack_mask(out["mask"][t], 10)
+        assert np.all(bb[~kept] == 0)
+        np.testing.assert_array_equal(out["beta"][t] != 0, bb != 0)
+        np.testing.assert_allclose(out["beta"][t], bb, atol=1e-6)
