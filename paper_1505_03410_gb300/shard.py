@@ -4,8 +4,10 @@ Every rank solves a contiguous share of the problems with ``lasso_batch`` on
 its own device; afterwards the host gathers the outputs on one rank.  The
 problems share nothing while they are solved (each one is its own path over
 the common design), so the data path has no collective: the only exchange is
-the gather of finished results.  Launch one process per GPU (torchrun) and
-initialise ``torch.distributed`` (NCCL or gloo) before calling.
+the gather of finished results.  Launch one process per GPU (torchrun), make
+each rank's GPU its current device (``torch.cuda.set_device``; NCCL's object
+gather needs it) and initialise ``torch.distributed`` (NCCL or gloo) before
+calling.
 """
 from __future__ import annotations
 
