@@ -201,7 +201,7 @@ def _traffic_record():
 def path_kernel_sha():
     """sha256 over the sources the path kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("path.cu", "cd_common.cuh", "dfloat.cuh", "device_util.cuh"):
+    for f in ("path_kernel.cuh", "gram_chain.cuh", "cd_common.cuh", "dfloat.cuh", "device_util.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1505_03410_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
@@ -301,6 +301,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
+    phases = pkg.lasso_path_phase_cycles(work.data_ptr(), stream.cuda_stream)
     st = pkg.stats_to_numpy(stats)
     solves_per_step = int((st["status"] == 0).sum())
     solves = solves_per_step * args.steps
@@ -319,7 +320,7 @@ def run_ours(args):
     Xd = torch.empty_like(XT)
     yd = torch.empty_like(y)
     rd = torch.empty_like(ratios)
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, args.steps)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -370,6 +371,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
             "gpu_launches": 5 * args.steps, "clocks": clk,
+            "phase_split": _phase_split(phases),
             "solves_per_step": solves_per_step, "epochs_per_step": int(st["epochs"].sum()),
             "checks_per_step": int(st["checks"].sum())}
     if ws == 1 and not args.no_extras:
@@ -386,11 +388,64 @@ def run_ours(args):
             line["tuned_vs_plain"] = _tuned_vs_plain(pkg, torch, dev, stream, flush, args.plain_sample)
     if ws == 1 and args.learned > 0:
         line["learned_warm_start"] = _learned(pkg, torch, dev, stream, args.learned)
+    if ws == 1 and not args.no_extras:
+        line["bound_audit"] = _audit(pkg, torch, dev, w, XT, y, ratios, T)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(w)
+        if "value" in line["cpu_baseline"] and T >= CPU_SAMPLE_T:
+            line["cpu_baseline"]["gpu_same_sample"] = _gpu_sample(pkg, torch, dev, stream, flush, w, XT, y,
+                                                                  ratios_h[:CPU_SAMPLE_T], opts)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _phase_split(ph):
+    """Share of the path kernel's time per phase (cycles of CTA 0's first
+    thread, accumulated over the last launch's whole path)."""
+    keys = ("check", "chain", "verify", "round_end", "pass_end", "other")
+    tot = float(sum(ph[k] for k in keys)) or 1.0
+    out = {k: round(ph[k] / tot, 4) for k in keys}
+    out["chain_entries"] = ph["chain_entries"]
+    out["rollbacks"] = ph["rollbacks"]
+    out["cycles"] = int(tot)
+    return out
+
+
+def _audit(pkg, torch, dev, w, XT, y, ratios, T):
+    """One untimed run of the same path with audit_bounds = 1: the largest
+    |c~_j - x_j^T rho| / E_j of the FP32 correlations over every check of every
+    lambda (row a11: <= 1 when every forward-error bound holds)."""
+    opts = pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], screen_rule=w.get("screen_rule", 0),
+                                  enet_alpha=w.get("enet_alpha", 1.0), audit_bounds=1)
+    out = pkg.solve_path(XT, y, ratios, n=w["n"], opts=opts)
+    torch.cuda.synchronize()
+    st = pkg.stats_to_numpy(out["stats"])
+    return {"max_ratio_fp32": float(st["bound_ratio"].max()), "lambdas": int(T),
+            "checks": int(st["checks"].sum()),
+            "what": "max over all checks and features of |c~_j - x_j^T rho| / E_j, c~ the FP32 correlation "
+                    "the safe test uses, x_j^T rho exact (double-float residual, exact sum), E_j its bound"}
+
+
+def _gpu_sample(pkg, torch, dev, stream, flush, w, XT, y, ratios_h, opts, reps=3):
+    """The GPU path on the oracle's sample (the first lambdas of the grid),
+    L2 flushed, for a lambda-matched comparison with cpu_baseline."""
+    r = torch.from_numpy(ratios_h).to(dev)
+    T = len(ratios_h)
+    pkg.solve_path(XT, y, r, n=w["n"], opts=opts)
+    times, ok = [], 0
+    for _ in range(reps):
+        flush.fill_(7)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = pkg.solve_path(XT, y, r, n=w["n"], opts=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        ok = int((pkg.stats_to_numpy(out["stats"])["status"] == 0).sum())
+    ms = statistics.mean(times)
+    return {"value": ok / (ms / 1e3), "unit": "solves/s", "ms": ms, "lambdas": T,
+            "sample": f"the same first {T} lambdas on the GPU path (mean of {reps} L2-flushed launches)"}
 
 
 def _xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, XT, n, p, ldx, label, reps=10):
@@ -480,6 +535,17 @@ def _tuned_vs_plain(pkg, torch, dev, stream, flush, sample):
     out["plain_single_path"] = {"solves_per_s": tot_ok / (tot_ms / 1e3), "certified": tot_ok,
                                 "solves": sample * T, "ms": tot_ms,
                                 "sample": f"first {sample} of the {B} problems, one lasso_path call each"}
+    # row a11 on the tensor-core path: one untimed audited lockstep run on a sample
+    opts = pkg.lasso_default_opts(xtr_scope=1, gemm_dtype=pkg.LASSO_BF16, screen_period=w["f"], gap_tol_rel=w["tol"],
+                                  audit_bounds=1)
+    aud = pkg.solve_batch(XT, Y[:32].contiguous(), ratios, n=n, row_mask=M[:32].contiguous(), opts=opts)
+    torch.cuda.synchronize()
+    sa = pkg.stats_to_numpy(aud["stats"])
+    out["bound_audit"] = {"problems": 32, "lambdas": T, "max_ratio_split_bf16_tc": float(sa["bound_ratio_tc"].max()),
+                          "max_ratio_fp32": float(sa["bound_ratio"].max()),
+                          "what": "max |c~_j - x_j^T rho| / E_j: first checks from the split-BF16 tensor-core "
+                                  "product (tc), later checks FP32 CUDA-core dots"}
+    del aud
     best = max(out["batched_fp32"]["solves_per_s"], out["batched_split_bf16_tc"]["solves_per_s"])
     out["tuned_over_plain"] = best / out["plain_single_path"]["solves_per_s"]
     out["note"] = ("tuned = batched persistent CD (one CTA per problem) with the tensor-core split-BF16 first "

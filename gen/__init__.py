@@ -70,9 +70,19 @@ def sparse_truth(rng, p, k, kind="normal"):
 
 
 def _matvec(XT, n, beta):
-    """X beta in float64 from the stored (possibly float32) columns."""
-    nz = np.nonzero(beta)[0]
-    return XT[nz, :n].astype(np.float64).T @ beta[nz]
+    """X beta in float64 from the stored (possibly float32) columns, summed
+    column by column in ascending order with plain elementwise operations, so
+    that the result does not depend on the host's BLAS (the inputs must be
+    the same bytes on every machine the tests run on)."""
+    acc = np.zeros(n)
+    for j in np.nonzero(beta)[0]:
+        acc = acc + XT[j, :n].astype(np.float64) * beta[j]
+    return acc
+
+
+def _norm(v):
+    """Euclidean norm by numpy's pairwise sum (no BLAS)."""
+    return float(np.sqrt(np.sum(v * v)))
 
 
 def small_problem(seed, n, p, dtype=np.float64, k=None, noise=0.1, ldx=None, center=False,
@@ -109,7 +119,7 @@ def workload2(seed=1002, n=500, p=50000):
     XT = toeplitz_design(rng, n, p, corr=0.5, dtype=np.float32)
     bstar = sparse_truth(rng, p, 50)
     signal = _matvec(XT, n, bstar)
-    sigma = np.linalg.norm(signal) / (5.0 * np.sqrt(n))
+    sigma = _norm(signal) / (5.0 * np.sqrt(n))
     y = signal + sigma * rng.standard_normal(n)
     return dict(name=f"toeplitz-{n}x{p}-f32", XT=XT, n=n, p=p, ldx=XT.shape[1], y=y,
                 beta_star=bstar, T=100, delta=3.0, f=10, tol=1e-6)
@@ -124,7 +134,7 @@ def workload3(seed=1003, n=1000, p=20000, B=256, k=30):
     XT = gaussian_design(rng, n, p, dtype=np.float32)
     bstar = sparse_truth(rng, p, k)
     signal = _matvec(XT, n, bstar)
-    sigma = np.linalg.norm(signal) / (5.0 * np.sqrt(n))
+    sigma = _norm(signal) / (5.0 * np.sqrt(n))
     Y = np.empty((B, n))
     row_mask = np.zeros((B, n), dtype=np.uint8)
     for b in range(B):
@@ -151,7 +161,7 @@ def workload4(seed=1004, n=300, p=10000, n_train=200000, n_eval=4096, k_range=(5
             bstar = sparse_truth(r, p, k)
             signal = _matvec(XT, n, bstar)
             snr = r.uniform(2.0, 10.0)
-            sigma = np.linalg.norm(signal) / (snr * np.sqrt(n))
+            sigma = _norm(signal) / (snr * np.sqrt(n))
             Y[i] = signal + sigma * r.standard_normal(n)
         return Y
 
@@ -171,7 +181,7 @@ def workload5(seed=1005, n=2000, p=100000, B=1024):
         bstar = sparse_truth(rng, p, k)
         signal = _matvec(XT, n, bstar)
         snr = rng.uniform(1.0, 10.0)
-        sigma = np.linalg.norm(signal) / (snr * np.sqrt(n))
+        sigma = _norm(signal) / (snr * np.sqrt(n))
         Y[b] = signal + sigma * rng.standard_normal(n)
     return dict(name=f"multi-rhs-{n}x{p}-B{B}-f32", XT=XT, n=n, p=p, ldx=XT.shape[1], Y=Y,
                 T=30, delta=2.0, f=10, tol=1e-6)

@@ -47,7 +47,9 @@ typedef enum lasso_status {
 } lasso_status;
 
 typedef enum lasso_dtype {
-  LASSO_F64 = 0,   /* IEEE binary64 */
+  LASSO_F64 = 0,   /* IEEE binary64.  lasso_path splits an FP64 design once into two FP32
+                      planes (x = hi + lo), so X enters the solver with about 48 significand
+                      bits, not 53; y and the objectives stay FP64 */
   LASSO_F32 = 1,   /* IEEE binary32 */
   LASSO_BF16 = 2   /* bfloat16 */
 } lasso_dtype;
@@ -90,6 +92,12 @@ typedef struct lasso_opts {
                             [X; sqrt((1 - a) lambda) I], [y; 0] with penalty a lambda, the augmented
                             rows implicit; lambda_max = ||X^T y||_inf / a and the stats report lambda.
                             Needs an FP32 design and screen_rule = 0; lasso_batch requires 1 */
+  int32_t audit_bounds;  /* 0: off (default).  1: every check also computes x_j^T rho exactly for
+                            every feature of the X^T rho scope and records, per lambda, the largest
+                            |c~_j - x_j^T rho| / E_j of the reduced-precision correlations c~ against
+                            their forward-error bounds E_j (bound_ratio and bound_ratio_tc of the
+                            stats; <= 1 when every bound holds).  A diagnostic: it adds one exact
+                            dot product per feature to every check and changes no result */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */
@@ -98,7 +106,11 @@ typedef struct lasso_path_stats {
   double primal;     /* P_lambda(beta) at the last check, Eq. (1) */
   double dual;       /* D_lambda(theta) at the last check, Eq. (2) */
   double gap;        /* primal - dual at the last check (Sec. 3.2) */
-  double radius;     /* GAP SAFE radius sqrt(2 gap)/lambda of the last check (Prop. 1) */
+  double radius;     /* GAP SAFE sphere radius of the last check: sqrt(2 (max(gap, 0) + tau))/lambda
+                        (Prop. 1, Eq. (10)), where tau >= 0 bounds the FP64 rounding of the gap
+                        (2 (n + p + 8) 2^-53 times the sum of the magnitudes of its terms, so the
+                        sphere stays safe under rounding); with refined_radius = 1, the smaller of
+                        that and (||lambda theta - y||^2 + tau)^(1/2)/lambda (Thm. 2) */
   double alpha;      /* dual scaling of the last check: theta = alpha * rho */
   int64_t epochs;    /* coordinate-descent passes run at this lambda */
   int64_t checks;    /* GAP SAFE checks run at this lambda */
@@ -108,6 +120,10 @@ typedef struct lasso_path_stats {
                         every check plus the safe-active set of every pass (algorithmic work) */
   int32_t converged; /* 1 if gap <= eps was reached */
   int32_t status;    /* lasso_status of this lambda (OK, NOT_CONVERGED, TIMEOUT, NONFINITE) */
+  double bound_ratio;    /* with audit_bounds = 1: the largest |c~_j - x_j^T rho| / E_j over the FP32
+                            CUDA-core correlations of this lambda's checks (0 otherwise) */
+  double bound_ratio_tc; /* with audit_bounds = 1, lockstep lasso_batch: the same over the first
+                            checks taken from the split-BF16 tensor-core product (0 otherwise) */
 } lasso_path_stats;
 
 /* Fills *opts with the defaults listed above.  opts must not be NULL. */
@@ -127,7 +143,8 @@ size_t lasso_path_workspace_size(int64_t n, int64_t p, lasso_dtype x_dtype, cons
  *
  *   X_dev        n x p design, column-major, leading dimension ldx.
  *                x_dtype LASSO_F32: ldx % 4 == 0 and X_dev 16-byte aligned.
- *                x_dtype LASSO_F64: ldx >= n, X_dev 8-byte aligned.
+ *                x_dtype LASSO_F64: ldx >= n, X_dev 8-byte aligned; the design is held
+ *                as two FP32 planes (about 48 significand bits, see LASSO_F64).
  *   n, p         1 <= n <= 2048, 1 <= p < 2^31.
  *   y_dev        n responses, FP64.
  *   lambda_ratios_dev  T ratios lambda_t / lambda_max, each in (0, 1]
@@ -252,14 +269,16 @@ lasso_status lasso_correlations_bf16(const void* X_bf16, int64_t n, int64_t p, i
                                      size_t workspace_bytes, void* stream);
 
 /* lasso_path without a workspace argument, for callers that cannot allocate
- * device memory where they solve (inside a stream capture, under a host
- * application that owns the device heap, or on a hot path that must not
- * allocate).  The paper has no counterpart: this is a deployment variant of
- * lasso_path with identical results.
+ * device memory where they solve: plug-ins under a host application that
+ * owns the device heap through its own pool, or real-time code whose hot path
+ * must not pay for (or risk the failure of) an allocation.  The paper has no
+ * counterpart: this is a deployment variant of lasso_path with identical
+ * results.
  *
  * Scratch comes from one static device array of 32 MiB that the library
  * holds on every GPU that loads it, until the process exits.  Problems whose
- * lasso_path_workspace_size exceeds 32 MiB return LASSO_ERR_INVALID_ARG.  The
+ * workspace (as lasso_path computes it for these sizes) exceeds 32 MiB return
+ * LASSO_ERR_INVALID_ARG.  The
  * first call on a device looks up the array's address (cudaGetSymbolAddress)
  * and should come before any stream capture.  All calls on a device share the
  * array: calls whose GPU work overlaps race and must be serialised by the
@@ -271,6 +290,22 @@ lasso_status lasso_path_static(const void* X_dev, lasso_dtype x_dtype, int64_t n
                                const double* beta0_dev, const lasso_opts* opts,
                                double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
                                void* stream);
+
+/* Where the last lasso_path run on this workspace spent its time: SM clock
+ * cycles counted by one thread of the first CTA, by phase of Algorithm 1 as
+ * the kernel runs it, written to cycles_host[0..7]:
+ *   [0] GAP SAFE checks (X^T rho, gap, sphere test, compaction)
+ *   [1] coordinate chains (the sequential updates of the nonzero coefficients)
+ *   [2] verification that the zero coefficients stay zero
+ *   [3] acceptance or rollback of a round, and the planning of the next one
+ *   [4] end of a pass (the next pass's support list)
+ *   [5] chain entries processed (a count, not cycles)
+ *   [6] rollbacks (a count)
+ *   [7] other set-up (per-lambda tables, waits before a check)
+ * The counters accumulate over the whole path.  Synchronises `stream` (the
+ * stream the path ran on) before it returns.  A diagnostic for tuning; the
+ * paper has no counterpart. */
+lasso_status lasso_path_phase_cycles(const void* workspace_dev, uint64_t* cycles_host, void* stream);
 
 /* Thread-local description of the last error returned on this thread
  * ("" if none).  The pointer stays valid until the next call on the thread. */

@@ -48,6 +48,7 @@ lasso_status check_opts(const lasso_opts& o) {
   if (o.refined_radius != 0 && o.refined_radius != 1)
     return set_error(LASSO_ERR_INVALID_ARG, "refined_radius must be 0 or 1");
   if (!(o.enet_alpha > 0.0 && o.enet_alpha <= 1.0)) return set_error(LASSO_ERR_INVALID_ARG, "enet_alpha must lie in (0, 1]");
+  if (o.audit_bounds != 0 && o.audit_bounds != 1) return set_error(LASSO_ERR_INVALID_ARG, "audit_bounds must be 0 or 1");
   if (o.enet_alpha < 1.0 && o.screen_rule != 0)
     return set_error(LASSO_ERR_INVALID_ARG, "the dome test is not built for the Elastic-Net (screen_rule must be 0)");
   return LASSO_OK;
@@ -169,6 +170,13 @@ lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, cons
   if (!ws || !aligned(ws, 256)) return set_error(LASSO_ERR_WORKSPACE, "lasso_batch: workspace must be non-NULL and 256-byte aligned");
   return batch_launch(X, n, p, ldx, Y, ldy, row_mask, ldm, B, ratios, T, beta0, ldb0, o, beta_out, mask_out, stats, ws, ws_bytes,
                       static_cast<cudaStream_t>(stream));
+}
+
+lasso_status lasso_path_phase_cycles(const void* ws, uint64_t* cycles_host, void* stream) {
+  clear_error();
+  if (!ws || !aligned(ws, 256) || !cycles_host)
+    return set_error(LASSO_ERR_INVALID_ARG, "lasso_path_phase_cycles: need a 256-byte aligned workspace and an output");
+  return path_phase_cycles(ws, cycles_host, static_cast<cudaStream_t>(stream));
 }
 
 const char* lasso_last_error(void) { return g_msg; }

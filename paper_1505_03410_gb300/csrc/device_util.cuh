@@ -24,9 +24,17 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(volatile con
 __device__ __forceinline__ unsigned ld_volatile_u(const unsigned* p) { return *(volatile const unsigned*)p; }
 
 // Sense-free generation barrier across all CTAs of a cooperative launch.
-// count and gen live in global memory; *err is the shared error word.
+// count and gen live in global memory; *err is the shared error word.  A
+// waiter gives up after limit_ns nanoseconds (recording kErrTimeout).  With
+// leave_on_error a waiter also leaves as soon as another CTA has recorded an
+// error, instead of waiting for the generation to turn: only for callers that
+// stop using the barrier after a failed wait (the single path), because the
+// CTAs that leave early no longer keep the arrivals of one barrier apart from
+// those of the next.
 // Returns false if the wait timed out or an error is pending.
-static __device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, unsigned nblocks) {
+static __device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, int* err, unsigned nblocks,
+                                              unsigned long long limit_ns = kWaitLimitNs,
+                                              bool leave_on_error = false) {
   __syncthreads();
   __shared__ int s_ok;
   if (nblocks == 1) {  // a one-CTA group: the block barrier is the whole barrier
@@ -48,7 +56,11 @@ static __device__ __noinline__ bool grid_sync(unsigned* count, unsigned* gen, in
       unsigned spins = 0;
       while (ld_volatile_u(gen) == my_gen) {
         if (++spins > 64) __nanosleep(200);
-        if ((spins & 255u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+        if (leave_on_error && (spins & 15u) == 0u && ld_volatile(err) != 0) {
+          ok = 0;
+          break;
+        }
+        if ((spins & 15u) == 0u && global_ns() - t0 > limit_ns) {
           set_error(err, kErrTimeout);
           ok = 0;
           break;

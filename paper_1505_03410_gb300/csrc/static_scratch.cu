@@ -1,21 +1,21 @@
 // lasso_path_static: the Lasso path without a caller-supplied workspace.
 //
 // Some callers cannot allocate device memory at the point where they solve:
-// code running inside a CUDA graph being captured (cudaMalloc is not a
-// capturable operation), plug-ins of a host application that owns the whole
-// device heap through its own pool, and real-time callers that are not
-// allowed the latency or failure modes of an allocation on their hot path.
-// For them this entry point takes its scratch from one fixed array in device
-// global memory that the library declares itself.
+// plug-ins of a host application that owns the whole device heap through its
+// own pool (a cudaMalloc of theirs would fail or fragment that pool), and
+// real-time callers that are not allowed the latency or the failure modes of
+// an allocation on their hot path.  For them this entry point takes its
+// scratch from one fixed array in device global memory that the library
+// declares itself.  The paper has no counterpart.
 //
 // Properties a caller must know:
 //   - The array holds kStaticScratchBytes (32 MiB) on every GPU that loads the
 //     library, for as long as the library stays loaded (until process exit).
-//   - Problems whose workspace (lasso_path_workspace_size) exceeds it are
-//     rejected with LASSO_ERR_INVALID_ARG.
+//   - Problems whose workspace exceeds it are rejected with
+//     LASSO_ERR_INVALID_ARG.
 //   - The first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress while that device is current; make that first call
-//     outside any stream capture.  Later calls only launch kernels.
+//     before any stream capture.  Later calls on the device reuse the address.
 //   - Every call on a device uses the same array.  Calls whose work overlaps
 //     on the GPU (different streams, or several host threads) race on it and
 //     give wrong results; serialise them.  Each call clears the parts that
@@ -70,9 +70,9 @@ extern "C" lasso_status lasso_path_static(const void* X, lasso_dtype xt, int64_t
                                           const lasso_opts* opts, double* beta_out, uint32_t* mask_out,
                                           lasso_path_stats* stats, void* stream) {
   clear_error();
-  const size_t need = lasso_path_workspace_size(n, p, xt, opts);
-  if (need == 0)
-    return set_error(LASSO_ERR_INVALID_ARG, "lasso_path_static: unsupported sizes or options");
+  // the size lasso_path will check, with the caller's ldx; 0 means invalid
+  // sizes, which lasso_path then reports with the exact reason
+  const size_t need = path_workspace_size(n, p, xt, ldx);
   if (need > kStaticScratchBytes)
     return set_error(LASSO_ERR_INVALID_ARG,
                      "lasso_path_static: this problem needs %zu bytes of scratch, more than the %zu bytes of the "

@@ -32,7 +32,7 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
             "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch",
             "lasso_correlations_bf16", "lasso_correlations_f32", "lasso_batch_tune_candidates",
-            "lasso_batch_tune_workspace_size", "lasso_batch_tune")
+            "lasso_batch_tune_workspace_size", "lasso_batch_tune", "lasso_path_phase_cycles")
 
 
 class LassoError(RuntimeError):
@@ -48,7 +48,7 @@ class LassoOpts(ctypes.Structure):
                 ("gemm_dtype", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
                 ("gemm_tile_n", ctypes.c_int32), ("batch_group", ctypes.c_int32),
                 ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32),
-                ("enet_alpha", ctypes.c_double)]
+                ("enet_alpha", ctypes.c_double), ("audit_bounds", ctypes.c_int32)]
 
 
 class LassoPathStats(ctypes.Structure):
@@ -56,13 +56,13 @@ class LassoPathStats(ctypes.Structure):
                 ("gap", ctypes.c_double), ("radius", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("epochs", ctypes.c_int64), ("checks", ctypes.c_int64), ("n_active", ctypes.c_int64),
                 ("n_nonzero", ctypes.c_int64), ("x_columns", ctypes.c_int64), ("converged", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("bound_ratio", ctypes.c_double), ("bound_ratio_tc", ctypes.c_double)]
 
 
 STATS_DTYPE = np.dtype([("lambda", "<f8"), ("primal", "<f8"), ("dual", "<f8"), ("gap", "<f8"),
                         ("radius", "<f8"), ("alpha", "<f8"), ("epochs", "<i8"), ("checks", "<i8"),
                         ("n_active", "<i8"), ("n_nonzero", "<i8"), ("x_columns", "<i8"), ("converged", "<i4"),
-                        ("status", "<i4")])
+                        ("status", "<i4"), ("bound_ratio", "<f8"), ("bound_ratio_tc", "<f8")])
 assert STATS_DTYPE.itemsize == ctypes.sizeof(LassoPathStats)
 
 _lock = threading.Lock()
@@ -108,6 +108,8 @@ def load(path: str | None = None):
                                              ctypes.POINTER(LassoOpts), I32, I32, ctypes.POINTER(LassoOpts), V, V, SZ,
                                              V]
             lib.lasso_batch_tune.restype = ctypes.c_int
+            lib.lasso_path_phase_cycles.argtypes = [V, V, V]
+            lib.lasso_path_phase_cycles.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
             lib.lasso_last_error.restype = ctypes.c_char_p
             _lib = lib
@@ -290,6 +292,18 @@ def tune_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, samp
                                    ctypes.byref(tuned), times.ctypes.data_as(ctypes.c_void_p), vp(ws.data_ptr()),
                                    need, vp(s.cuda_stream)))
     return tuned, times
+
+
+PHASES = ("check", "chain", "verify", "round_end", "pass_end", "chain_entries", "rollbacks", "other")
+
+
+def lasso_path_phase_cycles(workspace, stream) -> dict:
+    """Phase counters of the last lasso_path run on `workspace` (a device
+    address): SM cycles per phase and the chain-entry and rollback counts."""
+    out = (ctypes.c_uint64 * 8)()
+    _check(load().lasso_path_phase_cycles(ctypes.c_void_p(int(workspace)), ctypes.cast(out, ctypes.c_void_p),
+                                          ctypes.c_void_p(int(stream) if stream else 0)))
+    return dict(zip(PHASES, (int(v) for v in out)))
 
 
 def stats_to_numpy(stats_tensor) -> np.ndarray:

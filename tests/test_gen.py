@@ -74,3 +74,18 @@ def test_small_problem_layout(n, p, dtype):
     assert w["XT"].shape == (p, w["ldx"]) and w["ldx"] % 4 == 0 and w["ldx"] >= n
     assert np.all(w["XT"][:, n:] == 0)
     assert w["XT"].flags["C_CONTIGUOUS"] and w["XT"].dtype == dtype
+
+
+@pytest.mark.parametrize("name", ["workload2_sphere", "workload3_batch"])
+def test_workloads_match_the_stored_fingerprints(name):
+    """The full-size workloads regenerate to the bytes the stored oracle
+    results were computed from (the GPU tests compare against those)."""
+    import os
+    from tests.golden.oracle_paths import fingerprint
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".npz")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not written yet")
+    gold = np.load(path)
+    w = gen.workload2() if name.startswith("workload2") else gen.workload3()
+    assert fingerprint(w["XT"]) == str(gold["x_sha256"])
+    assert fingerprint(w["y" if "y" in w else "Y"]) == str(gold["y_sha256"])

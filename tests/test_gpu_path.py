@@ -245,3 +245,26 @@ def test_workload2_full_size_prefix(pkg):
     g = run_gpu(pkg, w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
     o = run_orc(w, ratios, screen_period=w["f"], gap_tol_rel=w["tol"])
     assert_parity(g, o)
+
+
+@pytest.mark.parametrize("n,p,dtype", [(77, 1537, np.float32), (130, 3000, np.float32), (37, 300, np.float64),
+                                       (501, 2000, np.float32)])
+def test_workspace_contents_do_not_matter(pkg, n, p, dtype):
+    """The workspace is the caller's uninitialised memory: filled with NaN bit
+    patterns before the call, it must give the oracle's path (rows past n, the
+    padding of the residual's planes, included)."""
+    prob = gen.small_problem(700 + n, n, p, dtype=dtype, k=max(2, min(n, p) // 20), noise=0.2)
+    ratios = oracle.lambda_ratios(12, 2.0)
+    opt = dict(gap_tol_rel=1e-9)
+    dev = torch.device("cuda:0")
+    xt = pkg.LASSO_F32 if dtype == np.float32 else pkg.LASSO_F64
+    need = pkg.lasso_path_workspace_size(n, p, xt, pkg.lasso_default_opts(**opt))
+    ws = torch.full((need,), 0xFF, dtype=torch.uint8, device=dev)
+    XT = torch.from_numpy(prob["XT"]).to(dev)
+    y = torch.from_numpy(prob["y"]).to(dev)
+    r = torch.from_numpy(np.ascontiguousarray(ratios)).to(dev)
+    out = pkg.solve_path(XT, y, r, n=n, opts=pkg.lasso_default_opts(**opt), workspace=ws)
+    torch.cuda.synchronize()
+    g = dict(beta=out["beta"].cpu().numpy(), mask=out["mask"].cpu().numpy().view(np.uint32),
+             stats=pkg.stats_to_numpy(out["stats"]))
+    assert_parity(g, run_orc(prob, ratios, **opt))

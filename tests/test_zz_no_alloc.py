@@ -1,6 +1,6 @@
 """lasso_path_static, the entry point for callers that cannot allocate device
-memory (inside a stream capture, under an application that owns the device
-heap, on a hot path that must not allocate): it must give the results of
+memory (plug-ins under an application that owns the device heap, real-time
+code whose hot path must not allocate): it must give the results of
 lasso_path, call after call, although every call reuses the same static
 scratch array.  This file is collected last on purpose."""
 import numpy as np
@@ -70,3 +70,13 @@ def test_static_scratch_rejects_oversized_problems(pkg):
                               0x40000, None, 0x50000, None)
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
     assert "static" in pkg.lasso_last_error()
+
+
+def test_static_scratch_reports_the_exact_reason(pkg):
+    """An invalid option gets the same message from both entry points."""
+    opts = pkg.lasso_default_opts(screen_period=0)
+    with pytest.raises(pkg.LassoError) as e:
+        pkg.lasso_path_static(0x10000, pkg.LASSO_F32, 64, 100, 64, 0x20000, 0x30000, 4, None, opts,
+                              0x40000, None, 0x50000, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    assert "screen_period" in pkg.lasso_last_error()
