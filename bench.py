@@ -384,6 +384,7 @@ def run_ours(args):
         line["xtr_pass"].append(_xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, Xbig, 2000, 100000, 2000,
                                           "gaussian-2000x100000-f32 (800 MB, the large multi-RHS design)"))
         del Xbig
+        line["tc_gemm"] = _tc_gemm(pkg, torch, dev, stream, flush, peaks)
         if not args.no_tuned:
             line["tuned_vs_plain"] = _tuned_vs_plain(pkg, torch, dev, stream, flush, args.plain_sample)
     if ws == 1 and args.learned > 0:
@@ -479,6 +480,43 @@ def _xtr_pass(pkg, torch, dev, stream, flush, peak, peak_src, XT, n, p, ldx, lab
             "launches": reps, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
             "l2": "flushed before each launch (512 MiB write, then a 256 MB read)"}
+
+
+def _tc_gemm(pkg, torch, dev, stream, flush, peaks, n=2000, p=100000, B=1024, reps=5):
+    """The batched correlation product of the large multi-RHS design on the
+    tensor cores, in the split-BF16 form the lockstep solver runs: K = 3L
+    (L = n rounded up to 8) BF16 rows [xh | xh | xl] against [rh | rl | rh].
+    Executed flops are 2 (3L) p B; the method's flops (one product X^T R) are
+    2 n p B.  L2 flushed before each launch."""
+    L = (n + 7) // 8 * 8
+    K = 3 * L
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    Xb = torch.randn((p, K), generator=g, device=dev, dtype=torch.float32).to(torch.bfloat16)
+    Rb = torch.randn((B, K), generator=g, device=dev, dtype=torch.float32).to(torch.bfloat16)
+    C = torch.empty((B, p), dtype=torch.float32, device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    times = []
+    for k in range(2 + reps):
+        flush.fill_(k & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.lasso_correlations_bf16(Xb.data_ptr(), K, p, K, Rb.data_ptr(), K, B, C.data_ptr(), p, ws.data_ptr(), 256,
+                                    stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    ex = 2.0 * K * p * B / (ms / 1e3) / 1e12
+    me = 2.0 * n * p * B / (ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops")
+    del Xb, Rb, C
+    return {"workload": f"split-BF16 X^T R, n={n} (K=3L={K}), p={p}, B={B}", "ms_per_launch": ms,
+            "executed_tflops": ex, "method_tflops": me, "peak_bf16_tflops": peak,
+            "frac_executed": ex / peak if peak else None,
+            "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if peak else "none",
+            "l2": "flushed before each launch"}
 
 
 def _tuned_vs_plain(pkg, torch, dev, stream, flush, sample):
