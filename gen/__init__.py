@@ -19,7 +19,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["round_up", "gaussian_design", "toeplitz_design", "sparse_truth", "WORKLOADS",
-           "workload1", "workload2", "workload3", "workload4", "workload5", "small_problem"]
+           "workload1", "workload2", "workload3", "workload4", "workload5", "small_problem", "sparse_problem"]
 
 
 def round_up(n, m):
@@ -95,6 +95,37 @@ def small_problem(seed, n, p, dtype=np.float64, k=None, noise=0.1, ldx=None, cen
     bstar = sparse_truth(rng, p, k)
     y = _matvec(XT, n, bstar) + noise * rng.standard_normal(n)
     return dict(XT=XT, n=n, p=p, ldx=XT.shape[1], y=y, beta_star=bstar)
+
+
+def sparse_problem(seed, n, p, density=0.05, k=None, noise=0.1, empty_cols=0):
+    """A sparse design with about density * n * p nonzeros (N(0,1) values at
+    uniform positions; every column unit-norm except `empty_cols` all-zero
+    columns), y = X beta* + noise.  Returns the dense column-major block XT
+    (p, n) float64 and the same matrix in compressed sparse column storage:
+    colptr (p+1,) int64, rowidx (nnz,) int32 ascending within each column,
+    values (nnz,) float64."""
+    rng = np.random.default_rng(seed)
+    XT = np.zeros((p, n))
+    nz = rng.random((p, n)) < density
+    XT[nz] = rng.standard_normal(int(nz.sum()))
+    for j in range(p):
+        if not XT[j].any():
+            XT[j, rng.integers(n)] = 1.0
+    if empty_cols:
+        XT[rng.choice(p, size=empty_cols, replace=False)] = 0.0
+    nrm = np.sqrt((XT * XT).sum(axis=1, keepdims=True))
+    nrm[nrm == 0] = 1.0
+    XT = XT / nrm
+    k = k if k is not None else max(1, min(p // 10, n // 2))
+    bstar = sparse_truth(rng, p, k)
+    y = _matvec(XT, n, bstar) + noise * rng.standard_normal(n)
+    counts = (XT != 0).sum(axis=1)
+    colptr = np.zeros(p + 1, dtype=np.int64)
+    colptr[1:] = np.cumsum(counts)
+    rows = [np.flatnonzero(XT[j]) for j in range(p)]
+    rowidx = np.concatenate(rows).astype(np.int32) if p else np.zeros(0, np.int32)
+    values = np.concatenate([XT[j, r] for j, r in enumerate(rows)]) if p else np.zeros(0)
+    return dict(XT=XT, n=n, p=p, ldx=n, y=y, beta_star=bstar, colptr=colptr, rowidx=rowidx, values=values)
 
 
 def workload1(seed=1001):

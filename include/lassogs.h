@@ -91,7 +91,8 @@ typedef struct lasso_opts {
                             + lambda (1 - a)/2 ||beta||^2 (the paper's appendix) as the Lasso on
                             [X; sqrt((1 - a) lambda) I], [y; 0] with penalty a lambda, the augmented
                             rows implicit; lambda_max = ||X^T y||_inf / a and the stats report lambda.
-                            Needs an FP32 design and screen_rule = 0; lasso_batch requires 1 */
+                            Both solvers, both design types and both screening rules take it (the
+                            dome is then the dome of the augmented problem) */
   int32_t audit_bounds;  /* 0: off (default).  1: every check also computes x_j^T rho exactly for
                             every feature of the X^T rho scope and records, per lambda, the largest
                             |c~_j - x_j^T rho| / E_j of the reduced-precision correlations c~ against
@@ -215,6 +216,31 @@ lasso_status lasso_batch(const float* X_dev, int64_t n, int64_t p, int64_t ldx, 
                          int32_t T, const double* beta0_dev, int64_t ldb0, const lasso_opts* opts,
                          double* beta_out_dev, uint32_t* mask_out_dev, lasso_path_stats* stats_dev,
                          void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* One Lasso path on a sparse design in compressed sparse column (CSC)
+ * storage -- the sparse variant of the solver of Sec. 4.1 (the paper's
+ * implementation runs on a dense Fortran-ordered or a sparse CSC design).
+ * Algorithm 1 as lasso_path computes it, with every option of lasso_opts
+ * except the batched solver's fields; the arithmetic is FP64 throughout (on
+ * sparse data the cost is gathers over the nonzeros, not flops).
+ *
+ *   colptr_dev   p + 1 int64: column j holds entries colptr[j] .. colptr[j+1]-1
+ *                (colptr[0] = 0, non-decreasing)
+ *   rowidx_dev   int32 row index of every entry, in [0, n) (any order within a column)
+ *   values_dev   FP64 value of every entry
+ *   n, p         1 <= n <= 16384, 1 <= p < 2^31
+ *   workspace    lasso_path_csc_workspace_size(n, p, opts) bytes, 256-byte aligned
+ *   Other arguments, outputs, asynchrony and errors as for lasso_path.  Row
+ *   indices out of range, NaN/Inf values or a decreasing colptr are found on
+ *   the device and reported as LASSO_ERR_INVALID_ARG in every record.  The
+ *   checks use all SMs; the coordinate passes run on one CTA, with the
+ *   residual in its shared memory. */
+size_t lasso_path_csc_workspace_size(int64_t n, int64_t p, const lasso_opts* opts);
+lasso_status lasso_path_csc(const int64_t* colptr_dev, const int32_t* rowidx_dev, const double* values_dev,
+                            int64_t n, int64_t p, const double* y_dev, const double* lambda_ratios_dev, int32_t T,
+                            const double* beta0_dev, const lasso_opts* opts, double* beta_out_dev,
+                            uint32_t* mask_out_dev, lasso_path_stats* stats_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream);
 
 /* Launch-shape autotuner for lasso_batch.  Times every candidate shape
  * (lasso_batch_tune_candidates() of them: per-CTA FP32 checks or lockstep

@@ -12,7 +12,8 @@ from .lassogs import (EXPORTED, LASSO_BF16, LASSO_ERR_CUDA, LASSO_ERR_INVALID_AR
                       lasso_path_workspace_size, load, solve_path, stats_to_numpy, lasso_batch,
                       lasso_batch_workspace_size, solve_batch, lasso_correlations_bf16,
                       lasso_correlations_f32, lasso_batch_tune, lasso_batch_tune_candidates,
-                      lasso_batch_tune_workspace_size, tune_batch, lasso_path_phase_cycles, PHASES)
+                      lasso_batch_tune_workspace_size, tune_batch, lasso_path_phase_cycles, PHASES,
+                      lasso_path_csc, lasso_path_csc_workspace_size, solve_path_csc)
 from .shard import problem_range, solve_batch_sharded  # noqa: F401  (one process per GPU)
 from . import lista  # noqa: F401  (learned warm start, include/lista.h)
 from .lista import ListaNet  # noqa: F401

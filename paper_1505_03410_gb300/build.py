@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblassogs.so")
-SOURCES = ["api.cu", "path.cu", "path_k_single_f32.cu", "path_k_single_f64.cu", "path_k_enet.cu", "path_k_batch.cu",
+SOURCES = ["api.cu", "path.cu", "path_k_single_f32.cu", "path_k_single_f64.cu", "path_k_enet.cu", "path_k_enet_f64.cu",
+           "path_k_batch.cu", "path_k_batch_enet.cu", "sparse_path.cu",
            "static_scratch.cu", "gemm_tc.cu", "lista.cu", "xtr.cu", "tune.cu"]
 HEADERS = ["dfloat.cuh", "device_util.cuh", "cd_common.cuh", "gram_chain.cuh", "path_kernel.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

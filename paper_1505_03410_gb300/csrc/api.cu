@@ -49,14 +49,14 @@ lasso_status check_opts(const lasso_opts& o) {
     return set_error(LASSO_ERR_INVALID_ARG, "refined_radius must be 0 or 1");
   if (!(o.enet_alpha > 0.0 && o.enet_alpha <= 1.0)) return set_error(LASSO_ERR_INVALID_ARG, "enet_alpha must lie in (0, 1]");
   if (o.audit_bounds != 0 && o.audit_bounds != 1) return set_error(LASSO_ERR_INVALID_ARG, "audit_bounds must be 0 or 1");
-  if (o.enet_alpha < 1.0 && o.screen_rule != 0)
-    return set_error(LASSO_ERR_INVALID_ARG, "the dome test is not built for the Elastic-Net (screen_rule must be 0)");
   return LASSO_OK;
 }
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 }  // namespace
+
+lasso_status check_options(const lasso_opts& o) { return check_opts(o); }
 }  // namespace lassogs
 
 using namespace lassogs;
@@ -111,8 +111,6 @@ lasso_status lasso_path(const void* X, lasso_dtype xt, int64_t n, int64_t p, int
   if (p < 1 || p > (int64_t)INT32_MAX / 4) return set_error(LASSO_ERR_INVALID_ARG, "lasso_path: p out of range (got %lld)", (long long)p);
   if (T < 1) return set_error(LASSO_ERR_INVALID_ARG, "lasso_path: T must be >= 1");
   if (ldx < n) return set_error(LASSO_ERR_INVALID_ARG, "lasso_path: ldx (%lld) < n (%lld)", (long long)ldx, (long long)n);
-  if (o.enet_alpha < 1.0 && xt != LASSO_F32)
-    return set_error(LASSO_ERR_INVALID_ARG, "lasso_path: enet_alpha < 1 needs an FP32 design");
   if (xt == LASSO_F32) {
     if (ldx % 4 != 0 || !aligned(X, 16))
       return set_error(LASSO_ERR_INVALID_ARG, "lasso_path: an FP32 design needs ldx %% 4 == 0 and a 16-byte aligned base");
@@ -151,8 +149,6 @@ lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, cons
   else lasso_default_opts(&o);
   lasso_status st = check_opts(o);
   if (st != LASSO_OK) return st;
-  if (o.enet_alpha != 1.0)
-    return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: the batched solver runs the Lasso only (enet_alpha = 1)");
   if (!X || !Y || !ratios || !beta_out || !stats)
     return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: X, Y, lambda_ratios, beta_out and stats must be non-NULL");
   if (n < 1 || n > kMaxRows) return set_error(LASSO_ERR_INVALID_ARG, "lasso_batch: need 1 <= n <= %lld", (long long)kMaxRows);

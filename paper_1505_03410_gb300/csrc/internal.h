@@ -14,6 +14,12 @@ constexpr int64_t kMaxRows = 2048;  // rows n supported by the register-resident
 lasso_status set_error(lasso_status code, const char* fmt, ...);
 void clear_error();
 
+// the option checks every entry point applies (message in lasso_last_error)
+lasso_status check_options(const lasso_opts& o);
+
+// time limit of the kernels' grid-barrier waits (20 s, or LASSOGS_WAIT_LIMIT_NS)
+unsigned long long wait_limit_ns();
+
 size_t path_workspace_size(int64_t n, int64_t p, lasso_dtype xt, int64_t ldx);
 lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, int64_t ldx, const double* y,
                          const double* ratios, int32_t T, const double* beta0, const lasso_opts& o,

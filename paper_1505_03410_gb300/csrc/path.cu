@@ -325,27 +325,10 @@ ChainShape chain_shape(int64_t n, bool batch) {
   return ChainShape{4, ld4 <= 128 ? 1 : (ld4 <= 256 ? 2 : 4)};
 }
 
-const void* pick_kernel(ChainShape c, bool xlo, bool batch, int per_sm = 1) {
-  if (batch) return path_kernel_batch(c.ngc, per_sm);
+const void* pick_kernel(ChainShape c, bool xlo, bool batch, int per_sm = 1, bool enet = false) {
+  if (batch) return enet ? path_kernel_batch_enet(c.ngc, per_sm) : path_kernel_batch(c.ngc, per_sm);
+  if (enet) return xlo ? path_kernel_enet_f64(c.ngc, c.cw) : path_kernel_enet(c.ngc, c.cw);
   return xlo ? path_kernel_single_f64(c.ngc, c.cw) : path_kernel_single_f32(c.ngc, c.cw);
-}
-
-// the single path on an FP32 design with the Elastic-Net's ridge term
-const void* pick_kernel_enet(ChainShape c) { return path_kernel_enet(c.ngc, c.cw); }
-
-// Time limit of the kernels' grid-barrier waits: 20 s, or the value of the
-// environment variable LASSOGS_WAIT_LIMIT_NS (nanoseconds, >= 1000) when it is
-// set.  The library's tests shorten it to make a wait run out on purpose and
-// check that the kernel reports LASSO_ERR_TIMEOUT and returns; it is not part
-// of the C ABI.
-unsigned long long wait_limit_ns() {
-  const char* v = std::getenv("LASSOGS_WAIT_LIMIT_NS");
-  if (v != nullptr) {
-    char* end = nullptr;
-    const unsigned long long x = std::strtoull(v, &end, 10);
-    if (end != v && x >= 1000ull) return x;
-  }
-  return kWaitLimitNs;
 }
 
 void fill_common(Args& a, int64_t n, int64_t p, int32_t T, const lasso_opts& o) {
@@ -394,6 +377,21 @@ int batch_grid(int64_t B, int sms, int per_sm = 2) {
 }
 
 }  // namespace
+
+// Time limit of the kernels' grid-barrier waits: 20 s, or the value of the
+// environment variable LASSOGS_WAIT_LIMIT_NS (nanoseconds, >= 1000) when it is
+// set.  The library's tests shorten it to make a wait run out on purpose and
+// check that the kernel reports LASSO_ERR_TIMEOUT and returns; it is not part
+// of the C ABI.
+unsigned long long wait_limit_ns() {
+  const char* v = std::getenv("LASSOGS_WAIT_LIMIT_NS");
+  if (v != nullptr) {
+    char* end = nullptr;
+    const unsigned long long x = std::strtoull(v, &end, 10);
+    if (end != v && x >= 1000ull) return x;
+  }
+  return kWaitLimitNs;
+}
 
 lasso_status path_phase_cycles(const void* ws, uint64_t* out, cudaStream_t stream) {
   static_assert(sizeof(((Ctrl*)nullptr)->prof) == 8 * sizeof(uint64_t), "eight phase counters");
@@ -445,8 +443,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + a.o_ctrl);
   const ChainShape cs = chain_shape(n, false);
   const bool enet = o.enet_alpha < 1.0;
-  if (enet && f64) return set_error(LASSO_ERR_INVALID_ARG, "enet_alpha < 1 needs an FP32 design");
-  const void* kfn = enet ? pick_kernel_enet(cs) : pick_kernel(cs, f64, false);
+  const void* kfn = pick_kernel(cs, f64, false, 1, enet);
   DevInfo d{};
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
@@ -590,7 +587,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   const ChainShape cs = chain_shape(n, true);
   const int per_sm = o.batch_ctas_per_sm == 1 ? 1 : 2;
   const int grid = batch_grid(B, d.sms, per_sm);  // <= the regions the layout holds
-  const void* kfn = pick_kernel(cs, false, true, per_sm);
+  const void* kfn = pick_kernel(cs, false, true, per_sm, o.enet_alpha < 1.0);
   const size_t dyn = dyn_smem(bl.L.s_cap, cs, false);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);

@@ -336,7 +336,8 @@ __device__ void batch_setup(const Args& a, Ctrl* ctl, char* wsb, int b, double* 
   __syncthreads();
   if (final) {
     if (tid == 0) {
-      ctl->lambda_max = __longlong_as_double((long long)ctl->m_bits);
+      // the Elastic-Net with mixing a: beta = 0 is optimal from ||X^T y||_inf / a
+      ctl->lambda_max = __ddiv_rn(__longlong_as_double((long long)ctl->m_bits), a.enet_alpha);
       ctl->m_bits = 0ull;
       ctl->eps = a.tol * ctl->yy;
       bool bad = !(ctl->lambda_max > 0.0);
@@ -1894,6 +1895,8 @@ const void* kernel_ptr() {
 const void* path_kernel_single_f32(int ngc, int cw);
 const void* path_kernel_single_f64(int ngc, int cw);
 const void* path_kernel_enet(int ngc, int cw);
+const void* path_kernel_enet_f64(int ngc, int cw);
 const void* path_kernel_batch(int ngc, int per_sm);
+const void* path_kernel_batch_enet(int ngc, int per_sm);
 
 }  // namespace lassogs

@@ -32,7 +32,8 @@ LASSO_F64, LASSO_F32, LASSO_BF16 = 0, 1, 2
 EXPORTED = ("lasso_default_opts", "lasso_lambda_grid", "lasso_path_workspace_size", "lasso_path",
             "lasso_last_error", "lasso_path_static", "lasso_batch_workspace_size", "lasso_batch",
             "lasso_correlations_bf16", "lasso_correlations_f32", "lasso_batch_tune_candidates",
-            "lasso_batch_tune_workspace_size", "lasso_batch_tune", "lasso_path_phase_cycles")
+            "lasso_batch_tune_workspace_size", "lasso_batch_tune", "lasso_path_phase_cycles",
+            "lasso_path_csc_workspace_size", "lasso_path_csc")
 
 
 class LassoError(RuntimeError):
@@ -108,6 +109,10 @@ def load(path: str | None = None):
                                              ctypes.POINTER(LassoOpts), I32, I32, ctypes.POINTER(LassoOpts), V, V, SZ,
                                              V]
             lib.lasso_batch_tune.restype = ctypes.c_int
+            lib.lasso_path_csc_workspace_size.argtypes = [I64, I64, ctypes.POINTER(LassoOpts)]
+            lib.lasso_path_csc_workspace_size.restype = SZ
+            lib.lasso_path_csc.argtypes = [V, V, V, I64, I64, V, V, I32, V, ctypes.POINTER(LassoOpts), V, V, V, V, SZ, V]
+            lib.lasso_path_csc.restype = ctypes.c_int
             lib.lasso_path_phase_cycles.argtypes = [V, V, V]
             lib.lasso_path_phase_cycles.restype = ctypes.c_int
             lib.lasso_last_error.argtypes = []
@@ -292,6 +297,46 @@ def tune_batch(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, samp
                                    ctypes.byref(tuned), times.ctypes.data_as(ctypes.c_void_p), vp(ws.data_ptr()),
                                    need, vp(s.cuda_stream)))
     return tuned, times
+
+
+def lasso_path_csc_workspace_size(n: int, p: int, opts: LassoOpts | None = None) -> int:
+    return int(load().lasso_path_csc_workspace_size(int(n), int(p), ctypes.byref(opts) if opts is not None else None))
+
+
+def lasso_path_csc(colptr, rowidx, values, n, p, y, lambda_ratios, T, beta0, opts, beta_out, mask_out, stats,
+                   workspace, workspace_bytes, stream) -> int:
+    """Direct call of the C entry point (pointer arguments are device addresses
+    or None).  Raises LassoError on a non-zero status."""
+    def vp(x):
+        return None if x is None else ctypes.c_void_p(int(x))
+    return _check(load().lasso_path_csc(vp(colptr), vp(rowidx), vp(values), int(n), int(p), vp(y),
+                                        vp(lambda_ratios), int(T), vp(beta0),
+                                        ctypes.byref(opts) if opts is not None else None, vp(beta_out),
+                                        vp(mask_out), vp(stats), vp(workspace), int(workspace_bytes),
+                                        ctypes.c_void_p(int(stream) if stream else 0)))
+
+
+def solve_path_csc(colptr, rowidx, values, y, ratios, n, beta0=None, opts=None, stream=None, want_mask=True):
+    """Allocate outputs and the workspace as torch CUDA tensors and run
+    lasso_path_csc.  colptr: (p+1,) int64, rowidx: (nnz,) int32, values:
+    (nnz,) float64, y: (n,) float64, ratios: (T,) float64 CUDA tensors."""
+    import torch
+    p = int(colptr.shape[0]) - 1
+    T = int(ratios.shape[0])
+    dev = colptr.device
+    opts = opts or lasso_default_opts()
+    words = (p + 31) // 32
+    beta_out = torch.empty((T, p), dtype=torch.float64, device=dev)
+    mask_out = torch.empty((T, words), dtype=torch.int32, device=dev) if want_mask else None
+    stats = torch.empty(T * STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    need = lasso_path_csc_workspace_size(n, p, opts)
+    workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    lasso_path_csc(colptr.data_ptr(), rowidx.data_ptr(), values.data_ptr(), n, p, y.data_ptr(), ratios.data_ptr(), T,
+                   beta0.data_ptr() if beta0 is not None else None, opts, beta_out.data_ptr(),
+                   mask_out.data_ptr() if mask_out is not None else None, stats.data_ptr(), workspace.data_ptr(),
+                   workspace.numel(), s.cuda_stream)
+    return dict(beta=beta_out, mask=mask_out, stats=stats, workspace=workspace)
 
 
 PHASES = ("check", "chain", "verify", "round_end", "pass_end", "chain_entries", "rollbacks", "other")

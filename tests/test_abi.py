@@ -164,19 +164,16 @@ def test_batch_group_needs_fp32_checks(pkg):
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
 
 
-def test_enet_restrictions(pkg):
-    """The Elastic-Net runs on the single path with an FP32 design and the
-    sphere test; the host rejects the rest before any CUDA call."""
-    o = pkg.lasso_default_opts(enet_alpha=0.5)
+@pytest.mark.parametrize("a", [0.0, -0.5, 1.5, float("nan")])
+def test_enet_alpha_out_of_range(pkg, a):
+    """The Elastic-Net's mixing a must lie in (0, 1]; the host rejects the
+    rest before any CUDA call, for both solvers."""
     with pytest.raises(pkg.LassoError) as e:
-        _call(pkg, opts=o, x_dtype=pkg.LASSO_F64)
-    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
-    with pytest.raises(pkg.LassoError) as e:
-        _call(pkg, opts=pkg.lasso_default_opts(enet_alpha=0.5, screen_rule=1))
+        _call(pkg, opts=pkg.lasso_default_opts(enet_alpha=a))
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
     with pytest.raises(pkg.LassoError) as e:
         pkg.lasso_batch(1 << 12, 10, 20, 12, 1 << 12, 10, None, 0, 2, 1 << 12, 3, None, 0,
-                        pkg.lasso_default_opts(enet_alpha=0.5, gemm_dtype=pkg.LASSO_F32), 1 << 12, None,
+                        pkg.lasso_default_opts(enet_alpha=a, gemm_dtype=pkg.LASSO_F32), 1 << 12, None,
                         1 << 12, 1 << 12, 1 << 20, None)
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
 

@@ -289,6 +289,21 @@ def test_batch_dome(pkg, gemm, group):
     check_batch(g, o)
 
 
+@pytest.mark.parametrize("gemm,group,a,rule", [(1, 1, 0.5, 0), (2, 1, 0.5, 0), (1, 8, 0.7, 0), (2, 1, 0.6, 1),
+                                                (1, 1, 0.4, 1)])
+def test_batch_enet(pkg, gemm, group, a, rule):
+    """The Elastic-Net in every batched mode (per-CTA FP32 checks, lockstep
+    split-BF16 first checks, groups of CTAs), with the sphere or the dome:
+    each problem is the augmented Lasso on its own rows, with its own
+    lambda_max = ||X_b^T y_b||_inf / a."""
+    prob, Y, rmask = _subsample_problem(208, 140, 1300, 6, correlated=True)
+    ratios = oracle.lambda_ratios(10, 2.0)
+    opt = dict(gap_tol_rel=1e-9, enet_alpha=a, screen_rule=rule)
+    g = run_gpu_batch(pkg, prob["XT"], 140, Y, rmask, ratios, gemm_dtype=gemm, batch_group=group, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=140, **opt)
+    check_batch(g, o)
+
+
 @pytest.mark.parametrize("gemm", GEMM)
 def test_batch_refined_radius(pkg, gemm):
     """Thm. 2's radius in the batched modes, from poor per-problem starting

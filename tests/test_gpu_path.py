@@ -165,6 +165,23 @@ def test_enet_parity(pkg, seed, n, p, a, opt):
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("seed,n,p,dtype,a,opt", [
+    (141, 90, 1100, np.float32, 0.5, dict(screen_rule=1)),          # the dome of the augmented problem
+    (142, 400, 2500, np.float32, 0.7, dict(screen_rule=1, refined_radius=1)),
+    (143, 64, 800, np.float64, 0.5, {}),                             # an FP64 design (two planes)
+    (144, 300, 1500, np.float64, 0.3, dict(screen_rule=1)),
+])
+def test_enet_dome_and_fp64(pkg, seed, n, p, dtype, a, opt):
+    """The Elastic-Net with the GAP SAFE dome (Eq. (11) on the augmented
+    problem) and on FP64 designs, against the oracle, which forms the
+    augmented design explicitly."""
+    prob = gen.small_problem(seed, n, p, dtype=dtype, k=max(2, min(n, p) // 20), noise=0.2, correlated=True)
+    ratios = oracle.lambda_ratios(12, 2.0)
+    g = run_gpu(pkg, prob, ratios, gap_tol_rel=1e-9, enet_alpha=a, **opt)
+    o = run_orc(prob, ratios, gap_tol_rel=1e-9, enet_alpha=a, **opt)
+    assert_parity(g, o)
+
+
 def test_enet_from_a_starting_point(pkg):
     """The Elastic-Net from an outside beta0 with warm starts off (every
     lambda restarts from it; the grid starts below lambda_max)."""
