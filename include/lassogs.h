@@ -73,10 +73,12 @@ typedef struct lasso_opts {
   int32_t gemm_tile_n;   /* lockstep batches: N tile of the tensor-core product, 64, 128 or 256
                             (0 = 128) */
   int32_t batch_group;   /* batched solver with gemm_dtype = LASSO_F32: CTAs per problem, 1..64
-                            (0 = 1).  A group splits the features of its problem into slices as
-                            the single path does; for designs that do not fit L2 it spreads each
-                            problem's column reads over several SMs.  lasso_batch_tune picks this,
-                            batch_ctas_per_sm, gemm_tile_n and gemm_dtype */
+                            (0 = 1).  A group solves its problem as lasso_path does with the
+                            grid: feature slices per CTA, and, when the group has more than
+                            ceil(n/256) CTAs, the coordinate chain in Gram form (a cache of
+                            x_i^T x_k over the support per group, at most max(512, n) features).
+                            lasso_batch_tune picks this, batch_ctas_per_sm, gemm_tile_n and
+                            gemm_dtype */
   int32_t screen_rule;   /* 0: GAP SAFE sphere, Eq. (10) (default); 1: sphere and GAP SAFE dome,
                             Eq. (11) with the appendix's parameters: a feature is screened when
                             either test screens it.  The dome lies inside the sphere, so it screens
@@ -245,7 +247,7 @@ lasso_status lasso_path_csc(const int64_t* colptr_dev, const int32_t* rowidx_dev
 /* Launch-shape autotuner for lasso_batch.  Times every candidate shape
  * (lasso_batch_tune_candidates() of them: per-CTA FP32 checks or lockstep
  * split-BF16 products, 1 or 2 solver CTAs per SM, for lockstep an N tile of
- * 128 or 256, for FP32 checks groups of 8 or 32 CTAs per problem) on the
+ * 128 or 256, for FP32 checks groups of 8, 16 or 32 CTAs per problem) on the
  * first `sample` problems over the first `lambdas`
  * ratios of the grid -- a warm-up run, then a run timed with CUDA events on
  * `stream` -- and writes *opts with the fastest gemm_dtype,

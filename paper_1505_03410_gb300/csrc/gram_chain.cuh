@@ -91,20 +91,34 @@ __device__ df2 warp_dot_col_rho(const float* colh, const float* coll, const floa
 }
 
 // Exact x_a^T x_b of two columns (each xh + xl when XLO; the product of the
-// two low parts, below 2^-48 of the total, is left out).  Whole warp.
+// two low parts, below 2^-48 of the total, is left out).  Whole warp.  rm
+// (nullptr: every row) restricts the sum to the rows i with rm[i] != 0 (the
+// row subset of a batched problem).
 template <int NG, bool XLO>
-__device__ df2 warp_dot_cols(const float* ah, const float* al, const float* bh, const float* bl, int ld4, int n) {
+__device__ df2 warp_dot_cols(const float* ah, const float* al, const float* bh, const float* bl, int ld4, int n,
+                             const uint8_t* rm = nullptr) {
   const int lane = threadIdx.x & 31;
   float S0 = 0.f, C0 = 0.f, S1 = 0.f, C1 = 0.f;
 #pragma unroll
   for (int k = 0; k < NG; ++k) {
     const int g = lane + 32 * k;
     if (g < ld4) {
-      const float4 x = ld_x4(ah, g, n);
+      float4 x = ld_x4(ah, g, n);
       const float4 y = ld_x4(bh, g, n);
+      if (rm != nullptr) {
+        const int r = 4 * g;
+        if (!rm[r]) x.x = 0.f;
+        if (r + 1 < n && !rm[r + 1]) x.y = 0.f;
+        if (r + 2 < n && !rm[r + 2]) x.z = 0.f;
+        if (r + 3 < n && !rm[r + 3]) x.w = 0.f;
+      }
       if (XLO) {
-        const float4 xl = ld_x4(al, g, n);
+        float4 xl = ld_x4(al, g, n);
         const float4 yl = ld_x4(bl, g, n);
+        if (x.x == 0.f) xl.x = 0.f;
+        if (x.y == 0.f) xl.y = 0.f;
+        if (x.z == 0.f) xl.z = 0.f;
+        if (x.w == 0.f) xl.w = 0.f;
         dot2_acc2(x.x, xl.x, y.x, yl.x, S0, C0);
         dot2_acc2(x.y, xl.y, y.y, yl.y, S1, C1);
         dot2_acc2(x.z, xl.z, y.z, yl.z, S0, C0);

@@ -199,17 +199,20 @@ enum {
   L_mref, L_msnap, L_cy, L_part_l2, L_gram, L_slot, L_feat, L_g0, L_dlt, L_N
 };
 
-// Slots of the Gram cache of the single path: twice the rows (a Lasso
-// solution in general position has at most n nonzeros), at least 512, at
-// most p.  gram = 0 leaves the cache out (the batched solver).
-int64_t gram_slots(int64_t n, int64_t p, bool gram) {
-  if (!gram) return 0;
-  return std::min<int64_t>(p, std::max<int64_t>(512, (2 * n + 31) / 32 * 32));
+// Slots of the Gram cache: twice the rows for the single path (a Lasso
+// solution in general position has at most n nonzeros), the rows for a group
+// of the batched solver (one cache per group), at least 512, at most p.
+// kGramNone leaves the cache out.
+enum GramKind { kGramNone = 0, kGramSingle = 1, kGramGroup = 2 };
+int64_t gram_slots(int64_t n, int64_t p, int gram) {
+  if (gram == kGramNone) return 0;
+  const int64_t rows = gram == kGramSingle ? 2 * n : n;
+  return std::min<int64_t>(p, std::max<int64_t>(512, (rows + 31) / 32 * 32));
 }
 
 // The residual rho (planes rho_h, rho_l) is snapshot 0 of the snapshot array:
 // the residual a round of passes starts from.
-Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes, bool gram = false) {
+Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes, int gram = kGramNone) {
   Layout L{};
   const long long ldw = (n + 3) / 4 * 4;
   const int s_cap = (int)std::min<int64_t>(s_cap_max, p);
@@ -250,10 +253,10 @@ Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes, bool gram =
   take(L_part_l2, sizeof(double) * kMaxGrid);
   const int64_t gc = gram_slots(n, p, gram);
   take(L_gram, sizeof(float2) * (size_t)gc * (size_t)gc);
-  take(L_slot, gram ? sizeof(int) * p : 0);
+  take(L_slot, gc ? sizeof(int) * p : 0);
   take(L_feat, sizeof(int) * (size_t)gc);
-  take(L_g0, gram ? sizeof(float2) * (s_cap + 1) : 0);
-  take(L_dlt, gram ? sizeof(float2) * (s_cap + 1) : 0);
+  take(L_g0, gc ? sizeof(float2) * (s_cap + 1) : 0);
+  take(L_dlt, gc ? sizeof(float2) * (s_cap + 1) : 0);
   L.gram_cap = (int)gc;
   L.region = off;
   L.planes = planes ? 2 * align256(sizeof(float) * (size_t)ldw * (size_t)p) : 0;
@@ -376,6 +379,11 @@ int batch_grid(int64_t B, int sms, int per_sm = 2) {
   return (int)std::min<int64_t>(B, std::min<int64_t>((int64_t)sms * per_sm, kMaxGrid));
 }
 
+// CTAs that rebuild the snapshots of a Gram round (256 rows each); a group of
+// the batched solver runs Gram rounds when it has more CTAs than these
+int snapshot_ctas(long long ldw) { return (int)((ldw + kFollowRows - 1) / kFollowRows); }
+bool group_gram(int64_t n, int group) { return group > 1 && group >= snapshot_ctas((n + 3) / 4 * 4) + 1; }
+
 }  // namespace
 
 // Time limit of the kernels' grid-barrier waits: 20 s, or the value of the
@@ -405,7 +413,7 @@ size_t path_workspace_size(int64_t n, int64_t p, lasso_dtype xt, int64_t ldx) {
   (void)ldx;
   if (n < 1 || n > kMaxRows || p < 1 || p > (int64_t)INT32_MAX / 4) return 0;
   if (xt != LASSO_F32 && xt != LASSO_F64) return 0;
-  return make_layout(n, p, kSCapPath, xt == LASSO_F64, true).total;
+  return make_layout(n, p, kSCapPath, xt == LASSO_F64, kGramSingle).total;
 }
 
 lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, int64_t ldx, const double* y,
@@ -413,7 +421,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
                          double* beta_out, uint32_t* mask_out, lasso_path_stats* stats, void* ws, size_t ws_bytes,
                          cudaStream_t stream) {
   const bool f64 = xt == LASSO_F64;
-  const Layout L = make_layout(n, p, kSCapPath, f64, true);
+  const Layout L = make_layout(n, p, kSCapPath, f64, kGramSingle);
   if (ws_bytes < L.total)
     return set_error(LASSO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes required", ws_bytes,
                      L.total);
@@ -461,7 +469,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
   const int fs = (int)((p + grid - 1) / grid);
   a.fs = (fs + 31) / 32 * 32;
   // CTAs 1..nsc rebuild the snapshots of Gram rounds (256 rows each)
-  a.nsc = (int)((a.ldw + kFollowRows - 1) / kFollowRows);
+  a.nsc = snapshot_ctas(a.ldw);
   if (a.nsc + 1 > grid) a.gram_cap = 0;
 
   CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream));
@@ -505,18 +513,23 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
 namespace {
 struct BatchLayout {
   Layout L;
-  int grid, regions;
+  int grid, regions, group;
   bool lockstep;
   long long Lk;  // K segment length of the split-BF16 operands
   size_t o_regions, o_x3, o_r3, o_c, o_gerr, total;
 };
 
-BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms) {
+// group > 1: groups of CTAs per problem, one workspace region per group (at
+// most 2 x SMs / group of them resident), each with its Gram cache when the
+// group is large enough for Gram rounds
+BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms, int group = 1) {
   BatchLayout bl{};
-  bl.L = make_layout(n, p, kSCapBatch, false);
+  const bool groups = !lockstep && group > 1;
+  bl.L = make_layout(n, p, kSCapBatch, false, groups && group_gram(n, group) ? kGramGroup : kGramNone);
   bl.grid = batch_grid(B, sms);
   bl.lockstep = lockstep;
-  bl.regions = lockstep ? (int)B : bl.grid;
+  bl.group = groups ? group : 1;
+  bl.regions = lockstep ? (int)B : groups ? (int)std::max<int64_t>(1, std::min<int64_t>(B, 2LL * sms / group)) : bl.grid;
   bl.Lk = (n + 7) / 8 * 8;
   size_t off = 256;
   bl.o_regions = off;
@@ -543,9 +556,9 @@ int device_sms() {
 }
 }  // namespace
 
-size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep) {
+size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep, int group) {
   if (n < 1 || n > kMaxRows || p < 1 || p > (int64_t)INT32_MAX / 4 || B < 1) return 0;
-  return batch_layout(n, p, B, lockstep, device_sms()).total;
+  return batch_layout(n, p, B, lockstep, device_sms(), group).total;
 }
 
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
@@ -557,7 +570,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
   const bool lockstep = o.gemm_dtype == LASSO_BF16;
-  const BatchLayout bl = batch_layout(n, p, B, lockstep, d.sms);
+  const BatchLayout bl = batch_layout(n, p, B, lockstep, d.sms, o.batch_group);
   if (ws_bytes < bl.total)
     return set_error(LASSO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes required", ws_bytes,
                      bl.total);
@@ -588,7 +601,9 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   const int per_sm = o.batch_ctas_per_sm == 1 ? 1 : 2;
   const int grid = batch_grid(B, d.sms, per_sm);  // <= the regions the layout holds
   const void* kfn = pick_kernel(cs, false, true, per_sm, o.enet_alpha < 1.0);
-  const size_t dyn = dyn_smem(bl.L.s_cap, cs, false);
+  // groups with Gram rounds hold the round's tables in shared memory
+  const size_t dyn = bl.L.gram_cap > 0 ? std::max(dyn_smem(bl.L.s_cap, cs, false), kGramSmemBytes)
+                                        : dyn_smem(bl.L.s_cap, cs, false);
   if (dyn + 8192 > (size_t)d.smem_optin)
     return set_error(LASSO_ERR_INVALID_ARG, "the chain ring of %zu bytes does not fit shared memory", dyn);
   CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
@@ -599,10 +614,11 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
     int occ = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, dyn));
     const int resident = d.sms * std::min(occ, per_sm);
-    const int groups = (int)std::min<int64_t>(B, resident / gs);
+    const int groups = (int)std::min<int64_t>(std::min<int64_t>(B, resident / gs), bl.regions);
     if (groups < 1)
       return set_error(LASSO_ERR_INVALID_ARG, "batch_group %d exceeds the %d resident CTAs", gs, resident);
     a.gsize = gs;
+    a.nsc = snapshot_ctas(a.ldw);  // a.gram_cap (from the layout) is 0 unless gs > nsc
     const long long fsz = (p + gs - 1) / gs;
     a.fs = (int)((fsz + 31) / 32 * 32);
     // each group's control block (its barrier count) starts at zero

@@ -673,14 +673,17 @@ __device__ void gram_round(const Args& a, char* wsb, Ctrl* ctl, unsigned char* d
 // recorded an error.
 constexpr int kFollowRows = 256;  // rows of one snapshot CTA
 template <bool XLO>
-__device__ void snapshot_follow(const Args& a, char* wsb, Ctrl* ctl, unsigned char* dsm, int nc, int part, int* err) {
+__device__ void snapshot_follow(const Args& a, char* wsb, Ctrl* ctl, unsigned char* dsm, int nc, int part, int* err,
+                                const uint8_t* rm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (warp >= 4) return;
   const unsigned FULL = 0xffffffffu;
   const int g2 = (kFollowRows / 2) * part + tid;  // float2 granule: rows 2 g2, 2 g2 + 1
   const int r0 = 2 * g2;
   const bool valid = r0 < a.ldw;  // ldw is a multiple of 4, so r0 + 1 < ldw too
-  const bool in0 = r0 < a.n, in1 = r0 + 1 < a.n;  // rows of the design (x is 0 below them)
+  // rows of the design (x is 0 below them) and of the problem's row subset
+  const bool in0 = r0 < a.n && (rm == nullptr || rm[r0] != 0);
+  const bool in1 = r0 + 1 < a.n && (rm == nullptr || rm[r0 + 1] != 0);
   float* snap = reinterpret_cast<float*>(wsb + a.o_snap);
   const int* chain = reinterpret_cast<const int*>(wsb + a.o_chain);
   const int* A = reinterpret_cast<const int*>(wsb + a.o_A);
@@ -801,6 +804,10 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   // G CTAs cooperate on one problem: the whole grid, or a group of the batch
   const int G = BATCH ? a.gsize : (int)gridDim.x;
   const int cta = (int)blockIdx.x % G, grp = (int)blockIdx.x / G;
+  // the single path's flow of rounds (planned rounds, Gram or direct form,
+  // snapshot 0 as the residual): the single path and groups of CTAs of the
+  // batched solver; one-CTA problems keep the residual in registers
+  const bool SP = !BATCH || G > 1;
   char* wsb = a.ws + (BATCH ? (size_t)grp * a.cta_bytes : (size_t)0);
 #define WS(T, name) reinterpret_cast<T*>(wsb + a.o_##name)
   Ctrl* ctl = WS(Ctrl, ctrl);
@@ -906,6 +913,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
     uint32_t* mout = a.mask_out ? a.mask_out + (size_t)b * a.T * a.words : nullptr;
     lasso_path_stats* sout = a.stats + (size_t)b * a.T;
     const uint32_t rbits = BATCH ? chain_row_bits<NGC, CW>(a, b) : 0xffffffffu;
+    const uint8_t* prm = (BATCH && a.rmask != nullptr) ? a.rmask + (size_t)b * a.ldm : nullptr;
     if (vload(*err) != 0) goto fail;  // NaN/Inf input or lambda_max = 0
 
   const int t_begin = (BATCH && a.lockstep) ? a.t0 : 0, t_end = (BATCH && a.lockstep) ? a.t1 : a.T;
@@ -1429,7 +1437,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
         // The Gram cache of the lambda (single path): after the first check
         // the slots 0..s-1 hold the support in ascending feature order, and
         // G[i][k] = x_i^T x_k for every pair of them (all CTAs)
-        if (!BATCH && a.gram_cap > 0 && checks == 1) {
+        if (SP && a.gram_cap > 0 && checks == 1) {
           if (s > a.gram_cap) {
             if (cta == 0 && tid == 0) {
               ctl->gram_on = 0;
@@ -1455,7 +1463,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               const int ji = __ldcg(WS(int, A) + __ldcg(sup + i)), jk = __ldcg(WS(int, A) + __ldcg(sup + k));
               const df2 v = warp_dot_cols<NG, XLO>(a.Xh + (long long)ji * a.ldx, XLO ? a.Xl + (long long)ji * a.ldx : nullptr,
                                                    a.Xh + (long long)jk * a.ldx, XLO ? a.Xl + (long long)jk * a.ldx : nullptr,
-                                                   a.ld4, a.n);
+                                                   a.ld4, a.n, prm);
               if (lane == 0) {
                 Gm[(size_t)i * a.gram_cap + k] = make_float2(v.h, v.l);
                 Gm[(size_t)k * a.gram_cap + i] = make_float2(v.h, v.l);
@@ -1508,7 +1516,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
             }
           }
         }
-        if constexpr (!BATCH) {
+        if (SP) {
           // the first round of the first pass (the residual of the removal is in snapshot 0)
           if (cta == 0) {
             __syncthreads();
@@ -1525,7 +1533,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
         }
         for (int e = 0; e < a.f && epochs < a.max_epochs; ++e) {
           // ---- one pass over the safe-active list, in rounds
-          if (BATCH && cta == 0) {
+          if (!SP && cta == 0) {
             load_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             if (tid == 0) {
               ctl->pos = 0;
@@ -1537,7 +1545,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           }
           for (;;) {
             PROF(7);
-            if constexpr (BATCH) {
+            if (!SP) {
               // R1 (CTA 0): chain = [forced entry] + the support positions of the
               // round's window [pos, pos + win) (at most s_cap of them).  The round
               // ends at the window's end, or at the first support position left out.
@@ -1588,7 +1596,8 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                     const df2 v = warp_dot_cols<NG, XLO>(a.Xh + (long long)jf * a.ldx,
                                                          XLO ? a.Xl + (long long)jf * a.ldx : nullptr,
                                                          a.Xh + (long long)jk * a.ldx,
-                                                         XLO ? a.Xl + (long long)jk * a.ldx : nullptr, a.ld4, a.n);
+                                                         XLO ? a.Xl + (long long)jk * a.ldx : nullptr, a.ld4, a.n,
+                                                         prm);
                     if (lane == 0) {
                       WS(float2, gram)[(size_t)newslot * a.gram_cap + k] = make_float2(v.h, v.l);
                       WS(float2, gram)[(size_t)k * a.gram_cap + newslot] = make_float2(v.h, v.l);
@@ -1600,7 +1609,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                 if (cta == 0)
                   gram_round<NG, XLO, EN>(a, wsb, ctl, dsm, gflags, ncr, newslot, df_from_double(rdg), err);
                 else if (cta <= a.nsc)
-                  snapshot_follow<XLO>(a, wsb, ctl, dsm, ncr, cta - 1, err);
+                  snapshot_follow<XLO>(a, wsb, ctl, dsm, ncr, cta - 1, err, prm);
               } else if (cta == 0 && ncr > 0) {
                 if (prof_thread) ctl->gprof[7] += 1ull;
                 // R1 in direct form (CTA 0), from snapshot 0
@@ -1738,13 +1747,13 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                   ctl->done = rend >= q ? 1 : 0;
                   ctl->win = (int)min((long long)q, 2ll * vload(ctl->win));
                 }
-                if constexpr (!BATCH) snap_to_front(nc);
+                if (SP) snap_to_front(nc);
               } else {
                 // chain entries before the entering position stand; later ones are undone
                 if (prof_thread) ctl->prof[6] += 1ull;
                 const int seg = lower_bound_i(WS(int, chain), nc, fst);
                 for (int c = seg + tid; c < nc; c += kThreads) WS(float2, bdf)[__ldcg(WS(int, A) + __ldcg(WS(int, chain) + c))] = WS(float2, oldb)[c];
-                if constexpr (BATCH) {
+                if (!SP) {
                   const float* sh = WS(float, snap) + (size_t)seg * 2 * a.ldw;
                   load_rho_regs<NGC, CW>(cx, sh, sh + a.ldw, rh, rl);
                 } else {
@@ -1777,8 +1786,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               __threadfence();
               __syncthreads();
               // the next round of the pass (single path)
-              if constexpr (!BATCH)
-                if (vload(ctl->done) == 0) plan_round(sup, s);
+              if (SP && vload(ctl->done) == 0) plan_round(sup, s);
             }
             GSYNC();
             PROF(3);
@@ -1787,7 +1795,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           // end of pass (CTA 0): write rho; next support list = survivors of the
           // old list merged with the entered positions (both ascending)
           if (cta == 0) {
-            if constexpr (BATCH) store_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
+            if (!SP) store_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
             const int ne = vload(ctl->n_entered);
             __syncthreads();
             int nsurv = 0;
@@ -1818,7 +1826,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
             __threadfence();
             __syncthreads();
             // single path: the first round of the next pass, if one follows
-            if (!BATCH && e + 1 < a.f && epochs + 1 < a.max_epochs) {
+            if (SP && e + 1 < a.f && epochs + 1 < a.max_epochs) {
               if (tid == 0) {
                 ctl->pos = 0;
                 ctl->sup_idx = 0;

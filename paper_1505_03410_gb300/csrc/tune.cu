@@ -4,7 +4,9 @@
 // the first check of each lambda gets X^T rho (per-CTA FP32 passes or one
 // split-BF16 tensor-core product per lambda), how many solver CTAs share an
 // SM (two, at 128 registers per thread, or one), the N tile of the
-// tensor-core product, and how many CTAs work on one problem (1, 8 or 32).
+// tensor-core product, and how many CTAs work on one problem (1, 8, 16 or
+// 32; a group larger than the CTAs that rebuild its snapshots runs the
+// coordinate chain in Gram form, as the single path does).
 // Every candidate makes the same screening decisions (each equals the FP64
 // test's), so the choice changes the time, never the result.  Each candidate
 // solves the same sample of problems over the first lambdas of the grid
@@ -28,6 +30,7 @@ struct Candidate {
 constexpr Candidate kCandidates[] = {
     {LASSO_F32, 2, 0, 1},    {LASSO_F32, 1, 0, 1},    {LASSO_BF16, 2, 128, 1}, {LASSO_BF16, 1, 128, 1},
     {LASSO_BF16, 2, 256, 1}, {LASSO_BF16, 1, 256, 1}, {LASSO_F32, 2, 0, 8},    {LASSO_F32, 2, 0, 32},
+    {LASSO_F32, 1, 0, 16},
 };
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
@@ -39,15 +42,21 @@ struct TuneLayout {
 
 TuneLayout tune_layout(int64_t n, int64_t p, int64_t sample, int32_t lambdas) {
   TuneLayout t{};
-  lasso_opts o;
-  lasso_default_opts(&o);
-  o.gemm_dtype = LASSO_BF16;
-  const size_t a = lasso_batch_workspace_size(n, p, sample, &o);
-  o.gemm_dtype = LASSO_F32;
-  const size_t b = lasso_batch_workspace_size(n, p, sample, &o);
-  if (a == 0 || b == 0) return t;
+  // the solver's workspace: the largest any candidate shape needs
+  size_t a = 0;
+  for (const Candidate& c : kCandidates) {
+    lasso_opts o;
+    lasso_default_opts(&o);
+    o.gemm_dtype = c.dtype;
+    o.batch_ctas_per_sm = c.per_sm;
+    o.gemm_tile_n = c.tile_n;
+    o.batch_group = c.group;
+    const size_t s = lasso_batch_workspace_size(n, p, sample, &o);
+    if (s == 0) return t;
+    a = std::max(a, s);
+  }
   t.solver = 0;
-  t.beta = a256(std::max(a, b));
+  t.beta = a256(a);
   t.stats = t.beta + a256(sizeof(double) * (size_t)sample * (size_t)lambdas * (size_t)p);
   t.total = t.stats + a256(sizeof(lasso_path_stats) * (size_t)sample * (size_t)lambdas);
   return t;

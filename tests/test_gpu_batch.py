@@ -202,10 +202,12 @@ def test_batch_captured_in_cuda_graph(pkg):
 
 
 def test_autotuner_picks_a_shape_and_keeps_results(pkg):
-    """lasso_batch_tune times its eight launch shapes and returns the fastest;
-    solving with the tuned options gives bit-identical coefficients, masks
-    and pass counts to the default shape (every shape makes the FP64 test's
-    decisions), and both match the oracle."""
+    """lasso_batch_tune times its nine launch shapes and returns the fastest;
+    solving with the tuned options gives the masks and pass counts of the
+    default shape (every shape makes the FP64 test's decisions) and the same
+    coefficients up to rounding (a group of CTAs may run the chain in Gram
+    form, which orders the double-float sums differently), and both match
+    the oracle."""
     prob, Y, rmask = _subsample_problem(209, 200, 2000, 40, correlated=False)
     ratios = oracle.lambda_ratios(8, 1.5)
     dev = torch.device("cuda:0")
@@ -219,7 +221,7 @@ def test_autotuner_picks_a_shape_and_keeps_results(pkg):
     k = int(np.argmin(np.where(times > 0, times, np.inf)))
     shapes = [(pkg.LASSO_F32, 2, 0, 1), (pkg.LASSO_F32, 1, 0, 1), (pkg.LASSO_BF16, 2, 128, 1),
               (pkg.LASSO_BF16, 1, 128, 1), (pkg.LASSO_BF16, 2, 256, 1), (pkg.LASSO_BF16, 1, 256, 1),
-              (pkg.LASSO_F32, 2, 0, 8), (pkg.LASSO_F32, 2, 0, 32)]
+              (pkg.LASSO_F32, 2, 0, 8), (pkg.LASSO_F32, 2, 0, 32), (pkg.LASSO_F32, 1, 0, 16)]
     assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n, tuned.batch_group) == shapes[k]
     assert tuned.gap_tol_rel == 1e-9
     outs = {}
@@ -228,7 +230,8 @@ def test_autotuner_picks_a_shape_and_keeps_results(pkg):
         torch.cuda.synchronize()
         st = pkg.stats_to_numpy(out["stats"]).reshape(40, len(ratios))
         outs[name] = (out["beta"].cpu().numpy(), out["mask"].cpu().numpy(), st)
-    np.testing.assert_array_equal(outs["default"][0], outs["tuned"][0])
+    np.testing.assert_allclose(outs["default"][0], outs["tuned"][0], rtol=0, atol=1e-10)
+    np.testing.assert_array_equal(outs["default"][0] != 0, outs["tuned"][0] != 0)
     np.testing.assert_array_equal(outs["default"][1], outs["tuned"][1])
     np.testing.assert_array_equal(outs["default"][2]["epochs"], outs["tuned"][2]["epochs"])
     pick = [0, 17, 39]

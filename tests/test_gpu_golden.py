@@ -105,13 +105,14 @@ def test_workload2_dome_every_lambda(pkg):
     _workload2(pkg, 1)
 
 
-@pytest.mark.parametrize("gemm", [2, 1])
-def test_workload3_every_problem_every_lambda(pkg, gemm):
+@pytest.mark.parametrize("gemm,group", [(2, 0), (1, 0), (1, 32)])
+def test_workload3_every_problem_every_lambda(pkg, gemm, group):
     """The 256 row-subset problems of the stability-selection workload
     (Gaussian 1000 x 20000, 50 lambdas to lambda_max/100), batched: lockstep
     with the split-BF16 tensor-core first check (gemm 2) and per-CTA FP32
     checks (gemm 1).  Counts, objectives, supports and masks of every
-    (problem, lambda); coefficients of 16 problems spread over the batch."""
+    (problem, lambda); coefficients of 16 problems spread over the batch.
+    With groups of 32 CTAs per problem the chain runs in Gram form."""
     gold = _load("workload3_batch")
     w = gen.workload3()
     assert fingerprint(w["XT"]) == str(gold["x_sha256"]), "the regenerated design differs from the stored one"
@@ -124,11 +125,12 @@ def test_workload3_every_problem_every_lambda(pkg, gemm):
     out = pkg.solve_batch(torch.from_numpy(w["XT"]).to(dev), torch.from_numpy(Y).to(dev),
                           torch.from_numpy(gold["ratios"]).to(dev), n=n,
                           row_mask=torch.from_numpy(w["row_mask"]).to(dev),
-                          opts=pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], gemm_dtype=gemm))
+                          opts=pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], gemm_dtype=gemm,
+                                                      batch_group=group))
     torch.cuda.synchronize()
     st = pkg.stats_to_numpy(out["stats"]).reshape(B, T)
     beta = out["beta"].cpu().numpy()
     mask = out["mask"].cpu().numpy().view(np.uint32)
     values = set(int(v) for v in gold["values_for"])
     for b in range(B):
-        _compare(f"workload3 gemm={gemm}", beta[b], mask[b], st[b], gold, b=b, values=b in values)
+        _compare(f"workload3 gemm={gemm} group={group}", beta[b], mask[b], st[b], gold, b=b, values=b in values)
