@@ -101,6 +101,16 @@ typedef struct lasso_opts {
                             their forward-error bounds E_j (bound_ratio and bound_ratio_tc of the
                             stats; <= 1 when every bound holds).  A diagnostic: it adds one exact
                             dot product per feature to every check and changes no result */
+  int32_t lockstep_pass; /* lockstep batches (gemm_dtype = LASSO_BF16): 0 (default) advances every
+                            problem by one lambda per launch, the product serving the first check
+                            of each lambda; 1 advances every problem by one coordinate pass per
+                            launch, with a product before every launch: every check reads it,
+                            and so does every pass, whose zero coefficients get their
+                            certificates anew from it (few column reads then remain).  The
+                            number of launches then depends on the data: lasso_batch reads a
+                            device counter of unfinished problems every 4 launches
+                            (synchronising `stream`), so such a call cannot be captured in a
+                            CUDA graph */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */
@@ -209,7 +219,9 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
  *               r ~ rh + rl, three BF16 GEMM terms, FP32 accumulation, error
  *               <= (3 2^-16 + 2^-20 + 3L 2^-24) |x||r|, L = n rounded up to 8),
  *               then one launch that advances every problem by one lambda
- *               (workspace: one region per problem plus the packed operands).
+ *               (workspace: one region per problem plus the packed operands);
+ *               with opts->lockstep_pass = 1, one product and one launch per
+ *               coordinate pass instead.
  * Either way the test decisions equal the exact ones: features the error
  * bound leaves undecided are recomputed exactly.  Results equal B calls of
  * lasso_path on the row-restricted problems, up to rounding. */
@@ -247,11 +259,12 @@ lasso_status lasso_path_csc(const int64_t* colptr_dev, const int32_t* rowidx_dev
 /* Launch-shape autotuner for lasso_batch.  Times every candidate shape
  * (lasso_batch_tune_candidates() of them: per-CTA FP32 checks or lockstep
  * split-BF16 products, 1 or 2 solver CTAs per SM, for lockstep an N tile of
- * 128 or 256, for FP32 checks groups of 8, 16 or 32 CTAs per problem) on the
+ * 128 or 256 and a product per lambda or per pass, for FP32 checks groups of
+ * 8, 16 or 32 CTAs per problem) on the
  * first `sample` problems over the first `lambdas`
  * ratios of the grid -- a warm-up run, then a run timed with CUDA events on
  * `stream` -- and writes *opts with the fastest gemm_dtype,
- * batch_ctas_per_sm, gemm_tile_n and batch_group to *tuned.  Every candidate makes the
+ * batch_ctas_per_sm, gemm_tile_n, batch_group and lockstep_pass to *tuned.  Every candidate makes the
  * same screening decisions (each equal to the FP64 test's), so the choice
  * changes the time, not the results.  Arguments as for lasso_batch;
  * 1 <= sample <= B, 1 <= lambdas <= T; times_ms (host, one float per

@@ -49,6 +49,8 @@ lasso_status check_opts(const lasso_opts& o) {
     return set_error(LASSO_ERR_INVALID_ARG, "refined_radius must be 0 or 1");
   if (!(o.enet_alpha > 0.0 && o.enet_alpha <= 1.0)) return set_error(LASSO_ERR_INVALID_ARG, "enet_alpha must lie in (0, 1]");
   if (o.audit_bounds != 0 && o.audit_bounds != 1) return set_error(LASSO_ERR_INVALID_ARG, "audit_bounds must be 0 or 1");
+  if (o.lockstep_pass != 0 && o.lockstep_pass != 1)
+    return set_error(LASSO_ERR_INVALID_ARG, "lockstep_pass must be 0 or 1");
   return LASSO_OK;
 }
 

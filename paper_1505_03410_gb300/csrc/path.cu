@@ -176,6 +176,8 @@ __global__ void pack_r_kernel(const double* Y, long long ldy, const uint8_t* rma
   }
 }
 
+__global__ void set_int_kernel(int* p, int v) { *p = v; }
+
 // ---------------------------------------------------------------- host side
 namespace {
 
@@ -196,7 +198,7 @@ struct Layout {
 enum {
   L_ctrl, L_cnt, L_part_l1, L_nrm, L_nrmf, L_ftab, L_bdf, L_b0df, L_rho0_h, L_rho0_l, L_ctil,
   L_mask, L_A, L_sup0, L_sup1, L_chain, L_entered, L_oldb, L_recs, L_snap, L_zl_j, L_zl_b, L_zbits, L_yb, L_sk,
-  L_mref, L_msnap, L_cy, L_part_l2, L_gram, L_slot, L_feat, L_g0, L_dlt, L_N
+  L_mref, L_msnap, L_cy, L_part_l2, L_gram, L_slot, L_feat, L_g0, L_dlt, L_anchor, L_dsnap, L_dref, L_N
 };
 
 // Slots of the Gram cache: twice the rows for the single path (a Lasso
@@ -257,6 +259,9 @@ Layout make_layout(int64_t n, int64_t p, int s_cap_max, bool planes, int gram = 
   take(L_feat, sizeof(int) * (size_t)gc);
   take(L_g0, gc ? sizeof(float2) * (s_cap + 1) : 0);
   take(L_dlt, gc ? sizeof(float2) * (s_cap + 1) : 0);
+  take(L_anchor, sizeof(float) * ldw);
+  take(L_dsnap, sizeof(float) * (s_cap + 2));
+  take(L_dref, sizeof(float) * p);
   L.gram_cap = (int)gc;
   L.region = off;
   L.planes = planes ? 2 * align256(sizeof(float) * (size_t)ldw * (size_t)p) : 0;
@@ -306,6 +311,9 @@ void set_offsets(Args& a, const Layout& L) {
   a.o_feat = L.o[L_feat];
   a.o_g0 = L.o[L_g0];
   a.o_dlt = L.o[L_dlt];
+  a.o_anchor = L.o[L_anchor];
+  a.o_dsnap = L.o[L_dsnap];
+  a.o_dref = L.o[L_dref];
   a.gram_cap = L.gram_cap;
   a.ldw = L.ldw;
   a.s_cap = L.s_cap;
@@ -650,6 +658,44 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   CUDA_TRY(cudaMemsetAsync(gerr, 0, 256, stream));
   pack_x_kernel<<<d.sms * 8, 256, 0, stream>>>(X, ldx, (int)n, (int)p, (int)Lk, X3);
   CUDA_TRY(cudaGetLastError());
+  if (o.lockstep_pass == 1) {
+    // one product and one launch per coordinate pass: the product is taken
+    // on the residuals every problem's next pass (or check) starts from
+    // (y at the first launch of a zero start; with beta0 that first launch
+    // forms rho inside and checks with its FP32 pass).  The launches stop
+    // when the counter of unfinished problems (read every 4 launches) is 0;
+    // each launch advances every unfinished problem, so a problem needs at
+    // most T (K + 1) of them.
+    int* active = gerr + 32;  // in the product's 256-byte error block, past the word it uses
+    set_int_kernel<<<1, 1, 0, stream>>>(active, (int)B);
+    CUDA_TRY(cudaGetLastError());
+    a.pass_mode = 1;
+    a.active = active;
+    const long long max_launches = (long long)T * (o.max_epochs + 1) + 1;
+    for (long long step = 0; step < max_launches; ++step) {
+      const bool use_gemm = !(step == 0 && beta0 != nullptr);
+      if (use_gemm) {
+        pack_r_kernel<<<d.sms * 4, 256, 0, stream>>>(Y, ldy, row_mask, ldm, a.ws, a.cta_bytes, a.o_rho_h, (int)n,
+                                                     (int)B, (int)Lk, step == 0 ? 1 : 0, R3);
+        CUDA_TRY(cudaGetLastError());
+        st = xtr_gemm_launch(X3, 3 * Lk, p, 3 * Lk, R3, 3 * Lk, B, C, p, gerr, stream, o.gemm_tile_n);
+        if (st != LASSO_OK) return st;
+      }
+      a.cfirst = use_gemm ? C : nullptr;
+      a.t0 = step == 0 ? 0 : 1;
+      a.t1 = T;
+      CUDA_TRY(cudaMemsetAsync(base, 0, 256, stream));
+      void* params[] = {&a};
+      CUDA_TRY(cudaLaunchKernel(kfn, dim3(grid), dim3(kThreads), params, dyn, stream));
+      if ((step & 3) == 3 || step + 1 == max_launches) {
+        int left = 0;
+        CUDA_TRY(cudaMemcpyAsync(&left, active, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        if (left <= 0) break;
+      }
+    }
+    return LASSO_OK;
+  }
   for (int t = 0; t < T; ++t) {
     // the product must be taken on the residual the lambda starts from: y at
     // t = 0 (zero start), rho0 = y - X beta0 when every lambda restarts, else

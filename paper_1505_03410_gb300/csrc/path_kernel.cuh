@@ -69,7 +69,9 @@ struct Ctrl {
   // Gram rounds in detail: [0] chain warp waiting for its helpers, [1] chain
   // warp busy, [2] helper warp 1 busy, [3] publisher busy, [4] snapshot CTA 1
   // waiting for published entries, [5] snapshot CTA 1 busy, [6] Gram rounds,
-  // [7] direct rounds
+  // [7] direct rounds.  One-CTA problems instead: [0] rounds, [1] positions
+  // scanned by the verification, [2] columns it read, [3] its exact
+  // refinements, [4] cycles of the snapshot distances
   unsigned long long gprof[8];
   int win;                    // positions a round may span (adaptive, see the passes)
   int prob;                   // groups of CTAs: the problem CTA 0 took from the queue
@@ -78,6 +80,13 @@ struct Ctrl {
   // an entering feature gets in it (-1 none) and the entries of the round
   // whose updates are published
   int nslots, gram_on, rmode, newslot, pub_g;
+  // lockstep batches advancing one pass per launch: the lambda index, whether
+  // the next launch resumes inside it, the next pass of the period, the
+  // support list in use (0: sup0, 1: sup1), the lambda's counters so far, and
+  // whether the path is finished
+  int t_cur, resume, e_cur, sup_par, pdone, scope_s;
+  float anorm;                // bound on ||anchor|| (one-CTA problems)
+  long long ep_s, ck_s, xc_s;
   // audit of the correlation bounds: largest |c~ - c| / E of the lambda so
   // far (FP64 bits), for CUDA-core and tensor-core correlations
   unsigned long long aud_bits, aud_tc_bits;
@@ -124,6 +133,12 @@ struct Args {
   // per problem (not per CTA), and the first check of each lambda reads
   // cfirst[j + b * ldc] with the forward-error factor cfactor
   int lockstep, t0, t1;
+  // pass_mode: each launch advances every problem by one pass (after the
+  // checks that are due), every check and the certificates of every pass
+  // come from cfirst, and t0 = 0 marks the first launch; active counts the
+  // problems whose path is not finished
+  int pass_mode;
+  int* active;
   const float* cfirst;
   long long ldc;
   float cfactor;
@@ -133,6 +148,10 @@ struct Args {
   // slot of a feature, feature of a slot, x_c^T rho_0 per chain entry, the
   // published update of each entry; nsc CTAs (1..nsc) rebuild the snapshots
   size_t o_gram, o_slot, o_feat, o_g0, o_dlt;
+  // one-CTA problems: the residual the certificates were last issued from
+  // (the anchor, high plane), the distance of each snapshot of a round from
+  // it, and the distance of the residual each certificate was issued at
+  size_t o_anchor, o_dsnap, o_dref;
   int gram_cap, nsc;
 };
 
@@ -885,10 +904,15 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                       WS(float, nrmf), WS(ChainRec, recs), WS(float2, oldb), WS(float, snap), WS(float, msnap)};
         if (a.t0 == 0) {
           batch_setup<XLO>(a, ctl, wsb, b, dbuf, 0, a.p, true, true, true);
-          if (tid == 0) ctl->failed = 0;
+          if (tid == 0) {
+            ctl->failed = 0;
+            ctl->t_cur = 0;
+            ctl->resume = 0;
+            ctl->pdone = 0;
+          }
           __syncthreads();
-        } else if (vload(ctl->failed) != 0) {
-          continue;  // its records were stamped when it failed
+        } else if (vload(ctl->failed) != 0 || (a.pass_mode && vload(ctl->pdone) != 0)) {
+          continue;  // its records were stamped when it failed, or its path is finished
         }
       } else if (G == 1) {
         batch_setup<XLO>(a, ctl, wsb, b, dbuf, 0, a.p, true, true, true);
@@ -916,7 +940,14 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
     const uint8_t* prm = (BATCH && a.rmask != nullptr) ? a.rmask + (size_t)b * a.ldm : nullptr;
     if (vload(*err) != 0) goto fail;  // NaN/Inf input or lambda_max = 0
 
-  const int t_begin = (BATCH && a.lockstep) ? a.t0 : 0, t_end = (BATCH && a.lockstep) ? a.t1 : a.T;
+  // pass mode: the problem continues at its own lambda, inside it when the
+  // last launch ended after a pass (resume); c~ of the product is valid until
+  // the residual changes in this launch (a pass, or a restart at a new lambda)
+  const bool PM = BATCH && a.lockstep && a.pass_mode;
+  const int t_begin = (BATCH && a.lockstep) ? (PM ? vload(ctl->t_cur) : a.t0) : 0;
+  const int t_end = (BATCH && a.lockstep) ? (PM ? a.T : a.t1) : a.T;
+  bool resume = PM && vload(ctl->resume) != 0;
+  bool cvalid = BATCH && a.cfirst != nullptr;
   for (int t = t_begin; t < t_end; ++t) {
     const double lam_path = __dmul_rn(vload(ctl->lambda_max), a.ratios[t]);
     // Elastic-Net (the paper's appendix): the Lasso with L1 weight a lambda on
@@ -941,432 +972,516 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
       const float2 b = ld_beta(cx, j);
       return __dmul_rn(rdg, __dadd_rn((double)b.x, (double)b.y));
     };
-    // per-lambda table lambda / ||x_j||^2; full mask; optional restart
-    for (int j = f0 + tid; j < f1; j += kThreads) {
-      float4 tb = WS(float4, ftab)[j];
-      if constexpr (EN) {
-        // 1 / ||x~_j||^2 of the augmented column, for this lambda
-        const double nr = __ldcg(WS(double, nrm) + j);
-        const double den = __dadd_rn(__dmul_rn(nr, nr), rdg);
-        const df2 iv = df_from_double(den > 0.0 ? __drcp_rn(den) : 0.0);
-        tb.x = iv.h;
-        tb.y = iv.l;
+    // per-lambda table lambda / ||x_j||^2; full mask; optional restart (a
+    // resumed lambda has them from its first launch)
+    if (!resume)
+      for (int j = f0 + tid; j < f1; j += kThreads) {
+        float4 tb = WS(float4, ftab)[j];
+        if constexpr (EN) {
+          // 1 / ||x~_j||^2 of the augmented column, for this lambda
+          const double nr = __ldcg(WS(double, nrm) + j);
+          const double den = __dadd_rn(__dmul_rn(nr, nr), rdg);
+          const df2 iv = df_from_double(den > 0.0 ? __drcp_rn(den) : 0.0);
+          tb.x = iv.h;
+          tb.y = iv.l;
+        }
+        const df2 thr = df_from_double(__dmul_rn(lam, __dadd_rn((double)tb.x, (double)tb.y)));
+        tb.z = thr.h;
+        tb.w = thr.l;
+        WS(float4, ftab)[j] = tb;
+        if (t > 0 && !a.warm_start) WS(float2, bdf)[j] = WS(float2, b0df)[j];
       }
-      const df2 thr = df_from_double(__dmul_rn(lam, __dadd_rn((double)tb.x, (double)tb.y)));
-      tb.z = thr.h;
-      tb.w = thr.l;
-      WS(float4, ftab)[j] = tb;
-      if (t > 0 && !a.warm_start) WS(float2, bdf)[j] = WS(float2, b0df)[j];
-    }
-    for (int w = wd0 + tid; w < wd1; w += kThreads) {
-      const int lo = w * 32, hi = min(a.p, lo + 32);
-      WS(uint32_t, mask)[w] = (hi - lo == 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
-    }
-    if (cta == 0 && t > 0 && !a.warm_start)
+    if (!resume)
+      for (int w = wd0 + tid; w < wd1; w += kThreads) {
+        const int lo = w * 32, hi = min(a.p, lo + 32);
+        WS(uint32_t, mask)[w] = (hi - lo == 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
+      }
+    if (cta == 0 && t > 0 && !a.warm_start && !resume)
       for (int i = tid; i < a.ldw; i += kThreads) {
         WS(float, rho_h)[i] = __ldcg(WS(float, rho0_h) + i);
         WS(float, rho_l)[i] = __ldcg(WS(float, rho0_l) + i);
       }
+    // the product of a pass-mode launch was taken on the residual before this restart
+    if (PM && t > 0 && !a.warm_start && !resume) cvalid = false;
     long long epochs = 0, checks = 0, xcols = 0;
     int scope_n = a.p;  // X^T rho scope of the next check
+    // pass mode: the next pass of the period when the lambda resumes, else the check first
+    int e_first = 0;
+    bool skip_check = false;
+    if (resume) {
+      epochs = vload(ctl->ep_s);
+      checks = vload(ctl->ck_s);
+      xcols = vload(ctl->xc_s);
+      scope_n = vload(ctl->scope_s);
+      e_first = vload(ctl->e_cur);
+      skip_check = e_first < a.f && epochs < a.max_epochs;
+      if (!skip_check) e_first = 0;
+    }
+    if (PM && cta == 0 && tid == 0) ctl->t_cur = t;
     GSYNC();
 
     for (;;) {
-      // ======================= CHECK =======================
-      PROF(7);
-      // (C1) ||rho||^2, y^T rho (every CTA), c~ for the slice, sum |beta| of the slice
-      double rr = 0.0, yr = 0.0;
-      for (int i = tid; i < a.n; i += kThreads) {
-        const double r = __dadd_rn((double)__ldcg(WS(float, rho_h) + i), (double)__ldcg(WS(float, rho_l) + i));
-        rr = __fma_rn(r, r, rr);
-        yr = __fma_rn(yv[i], r, yr);
-      }
-      rr = block_sum_d(rr, dbuf);
-      yr = block_sum_d(yr, dbuf);
-      const float rnormf = __fmul_ru(__fsqrt_ru(__double2float_ru(rr)), 1.0001f);
-      {
-        float4 r4[NG];
-#pragma unroll
-        for (int k = 0; k < NG; ++k) {
-          const int g = lane + 32 * k;
-          r4[k] = (g < a.ld4) ? ldcg4(WS(float, rho_h), g) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!skip_check) {
+        // ======================= CHECK =======================
+        PROF(7);
+        // (C1) ||rho||^2, y^T rho (every CTA), c~ for the slice, sum |beta| of the slice
+        double rr = 0.0, yr = 0.0;
+        for (int i = tid; i < a.n; i += kThreads) {
+          const double r = __dadd_rn((double)__ldcg(WS(float, rho_h) + i), (double)__ldcg(WS(float, rho_l) + i));
+          rr = __fma_rn(r, r, rr);
+          yr = __fma_rn(yv[i], r, yr);
         }
-        float mlo = 0.f;
-        double aud = 0.0, aud_tc = 0.0;
-        // the first check of a lambda of a lockstep batch takes c~ from the
-        // batched tensor-core product, with its own error factor
-        const bool from_gemm = BATCH && a.cfirst != nullptr && checks == 0;
-        bfc = from_gemm ? a.cfactor : bf;
-        for (int j = f0 + warp; j < f1; j += nwarps) {
-          const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
-          float c = 0.f;
-          if (in) {
-            c = from_gemm ? __ldcg(a.cfirst + (size_t)j + (size_t)b * a.ldc)
-                          : warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-            float E = __fmul_ru(__fmul_ru(bfc, __ldcg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
-            if constexpr (EN) {
-              const float bh = ld_beta(cx, j).x;
-              if (bh != 0.f) c = __fsub_rn(c, __fmul_rn(rdgf, bh));  // x~_j^T rho~
-              E = __fadd_ru(E, ridge_err(j, c));
-            }
-            mlo = fmaxf(mlo, __fsub_rd(fabsf(c), E));
-            if (a.audit) {
-              // the exact correlation (double-float residual, exact sum) against c~ and its bound
-              const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l),
-                                                     __fmul_ru(__ldcg(WS(float, nrmf) + j), rnormf));
-              double cv = df_to_double(ce);
-              if constexpr (EN) cv = __dsub_rn(cv, ridge_exact(j));
-              const double ratio = fabs(__dsub_rn((double)c, cv)) / (double)E;
-              if (from_gemm) aud_tc = fmax(aud_tc, ratio);
-              else aud = fmax(aud, ratio);
-            }
+        rr = block_sum_d(rr, dbuf);
+        yr = block_sum_d(yr, dbuf);
+        const float rnormf = __fmul_ru(__fsqrt_ru(__double2float_ru(rr)), 1.0001f);
+        {
+          float4 r4[NG];
+  #pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            const int g = lane + 32 * k;
+            r4[k] = (g < a.ld4) ? ldcg4(WS(float, rho_h), g) : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          if (lane == 0) WS(float, ctil)[j] = c;
-        }
-        if (lane == 0) atomicMax(&ctl->mlo_bits, __float_as_uint(fmaxf(mlo, 0.f)));
-        if (a.audit && lane == 0) {
-          atomicMax(&ctl->aud_bits, (unsigned long long)__double_as_longlong(aud));
-          atomicMax(&ctl->aud_tc_bits, (unsigned long long)__double_as_longlong(aud_tc));
-        }
-        double l1p = 0.0, l2p = 0.0;
-        for (int j = f0 + tid; j < f1; j += kThreads) {
-          const float2 b = ld_beta(cx, j);
-          const double bv = __dadd_rn((double)b.x, (double)b.y);
-          l1p = __dadd_rn(l1p, fabs(bv));
-          if constexpr (EN) l2p = __fma_rn(bv, bv, l2p);
-        }
-        l1p = block_sum_d(l1p, dbuf);
-        if (tid == 0) WS(double, part_l1)[cta] = l1p;
-        if constexpr (EN) {
-          l2p = block_sum_d(l2p, dbuf);
-          if (tid == 0) WS(double, part_l2)[cta] = l2p;
-        }
-      }
-      GSYNC();
-      // (C2) exact refinement of the candidates for the maximum
-      {
-        const float mlo = __uint_as_float(vload(ctl->mlo_bits));
-        for (int j = f0 + warp; j < f1; j += nwarps) {
-          const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
-          if (!in) continue;
-          const float c = __ldcg(WS(float, ctil) + j);
-          const float nf = __ldcg(WS(float, nrmf) + j);
-          float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
-          if constexpr (EN) E = __fadd_ru(E, ridge_err(j, c));
-          if (__fadd_ru(fabsf(c), E) >= mlo) {
-            const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l), __fmul_ru(nf, rnormf));
-            double cv = df_to_double(ce);
-            if constexpr (EN) cv = __dsub_rn(cv, ridge_exact(j));
-            cv = fabs(cv);
-            if (lane == 0) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(cv));
+          float mlo = 0.f;
+          double aud = 0.0, aud_tc = 0.0;
+          // the first check of a lambda of a lockstep batch takes c~ from the
+          // batched tensor-core product, with its own error factor
+          const bool from_gemm = cvalid && (PM || checks == 0);
+          bfc = from_gemm ? a.cfactor : bf;
+          for (int j = f0 + warp; j < f1; j += nwarps) {
+            const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
+            float c = 0.f;
+            if (in) {
+              c = from_gemm ? __ldcg(a.cfirst + (size_t)j + (size_t)b * a.ldc)
+                            : warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
+              float E = __fmul_ru(__fmul_ru(bfc, __ldcg(WS(float, nrmf) + j)), rnormf) + 1e-37f;
+              if constexpr (EN) {
+                const float bh = ld_beta(cx, j).x;
+                if (bh != 0.f) c = __fsub_rn(c, __fmul_rn(rdgf, bh));  // x~_j^T rho~
+                E = __fadd_ru(E, ridge_err(j, c));
+              }
+              mlo = fmaxf(mlo, __fsub_rd(fabsf(c), E));
+              if (a.audit) {
+                // the exact correlation (double-float residual, exact sum) against c~ and its bound
+                const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l),
+                                                       __fmul_ru(__ldcg(WS(float, nrmf) + j), rnormf));
+                double cv = df_to_double(ce);
+                if constexpr (EN) cv = __dsub_rn(cv, ridge_exact(j));
+                const double ratio = fabs(__dsub_rn((double)c, cv)) / (double)E;
+                if (from_gemm) aud_tc = fmax(aud_tc, ratio);
+                else aud = fmax(aud, ratio);
+              }
+            }
+            if (lane == 0) WS(float, ctil)[j] = c;
+          }
+          if (lane == 0) atomicMax(&ctl->mlo_bits, __float_as_uint(fmaxf(mlo, 0.f)));
+          if (a.audit && lane == 0) {
+            atomicMax(&ctl->aud_bits, (unsigned long long)__double_as_longlong(aud));
+            atomicMax(&ctl->aud_tc_bits, (unsigned long long)__double_as_longlong(aud_tc));
+          }
+          double l1p = 0.0, l2p = 0.0;
+          for (int j = f0 + tid; j < f1; j += kThreads) {
+            const float2 b = ld_beta(cx, j);
+            const double bv = __dadd_rn((double)b.x, (double)b.y);
+            l1p = __dadd_rn(l1p, fabs(bv));
+            if constexpr (EN) l2p = __fma_rn(bv, bv, l2p);
+          }
+          l1p = block_sum_d(l1p, dbuf);
+          if (tid == 0) WS(double, part_l1)[cta] = l1p;
+          if constexpr (EN) {
+            l2p = block_sum_d(l2p, dbuf);
+            if (tid == 0) WS(double, part_l2)[cta] = l2p;
           }
         }
-      }
-      GSYNC();
-      // (C3) objectives, gap, radius (identical in every CTA); sphere test on the slice
-      double l1 = 0.0;
-      for (int c = tid; c < G; c += kThreads) l1 = __dadd_rn(l1, __ldcg(WS(double, part_l1) + c));
-      l1 = block_sum_d(l1, dbuf);
-      double l2 = 0.0;
-      if constexpr (EN) {
-        // ||rho~||^2 = ||rho||^2 + mu ||beta||^2
-        for (int c = tid; c < G; c += kThreads) l2 = __dadd_rn(l2, __ldcg(WS(double, part_l2) + c));
-        l2 = block_sum_d(l2, dbuf);
-        rr = __dadd_rn(rr, __dmul_rn(rdg, l2));
-      }
-      const double m = __longlong_as_double((long long)vload(ctl->m_bits));
-      double alpha;
-      if (a.dual_point == 0) {
-        alpha = __drcp_rn(lam > m ? lam : m);
-      } else if (rr == 0.0) {
-        alpha = 0.0;
-      } else {
-        double al = __ddiv_rn(yr, __dmul_rn(lam, rr));
-        if (m > 0.0) {
-          const double lim = __drcp_rn(m);
-          if (al < -lim) al = -lim;
-          if (al > lim) al = lim;
-        }
-        alpha = al;
-      }
-      double d2 = 0.0;
-      for (int i = tid; i < a.n; i += kThreads) {
-        const double r = __dadd_rn((double)__ldcg(WS(float, rho_h) + i), (double)__ldcg(WS(float, rho_l) + i));
-        const double dd = __dsub_rn(__dmul_rn(lam, __dmul_rn(alpha, r)), yv[i]);
-        d2 = __fma_rn(dd, dd, d2);
-      }
-      d2 = block_sum_d(d2, dbuf);
-      if constexpr (EN) {
-        // the augmented rows: (lambda alpha (-sqrt(mu) beta_j))^2
-        const double la = __dmul_rn(lam, alpha);
-        d2 = __dadd_rn(d2, __dmul_rn(__dmul_rn(la, la), __dmul_rn(rdg, l2)));
-      }
-      const double yy = vload(ctl->yy);
-      const double P = __dadd_rn(__dmul_rn(0.5, rr), __dmul_rn(lam, l1));
-      const double D = __dsub_rn(__dmul_rn(0.5, yy), __dmul_rn(0.5, d2));
-      const double Gap = __dsub_rn(P, D);
-      const double tau = 2.0 * (double)(a.n + a.p + (EN ? a.p : 0) + 8) * u64 * (rr + lam * l1 + yy + d2);
-      const double Gs = (Gap > 0.0 ? Gap : 0.0) + tau;
-      double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
-      if (a.refined_radius == 1) {
-        // Thm. 2's radius (R^2 - r(beta)^2)^(1/2): sqrt(2 G)/lambda, or R =
-        // ||theta - y/lambda|| when the clipped r(beta) is 0 (P > ||y||^2/2)
-        const double Rt = __ddiv_rn(__dsqrt_rn(__dadd_rn(d2, tau)), lam);
-        if (Rt < rad) rad = Rt;
-      }
-      const double aa = fabs(alpha);
-      // GAP SAFE dome (Eq. (11), parameters of the appendix): center
-      // (y/lambda + theta)/2, radius R/2 with R = ||y/lambda - theta||, unit
-      // normal (y/lambda - theta)/R, ratio 2 r^2/R^2 - 1 with r the radius of
-      // Thm. 2 from the primal point; lambda^2 R^2 is enlarged and lambda^2 r^2
-      // reduced by the rounding bound tau, as the sphere's gap is.  When
-      // theta = y/lambda the dome is a point and only the sphere runs.
-      const bool dome = a.screen_rule == 1 && d2 > 0.0;
-      double drad = 0.0, dal = 0.0, dR = 1.0;
-      if (dome) {
-        const double big = __dadd_rn(d2, tau);
-        double small = __dsub_rn(__dsub_rn(yy, __dmul_rn(2.0, P)), tau);
-        if (small < 0.0) small = 0.0;
-        double q = __ddiv_rn(small, big);
-        if (q > 1.0) q = 1.0;
-        dal = __dsub_rn(__dmul_rn(2.0, q), 1.0);
-        drad = __ddiv_rn(__dmul_rn(0.5, __dsqrt_rn(big)), lam);
-        dR = __ddiv_rn(__dsqrt_rn(d2), lam);
-      }
-      ++checks;
-      xcols += scope_n;
-      const bool stop = Gap <= vload(ctl->eps);
-      const bool cap = epochs >= a.max_epochs;
-      {
-        const float aaf_lo = __double2float_rd(aa), aaf_hi = __double2float_ru(aa);
-        const float radf_lo = __double2float_rd(rad), radf_hi = __double2float_ru(rad);
-        int kept = 0, sup = 0, nnz = 0, zero = 0;
-        // each warp handles 32 consecutive features = one mask word
-        for (int w0 = f0 + 32 * warp; w0 < f1; w0 += 32 * nwarps) {
-          const int j = w0 + lane;
-          const bool valid = j < f1;
-          const uint32_t word = __ldcg(WS(uint32_t, mask) + (w0 >> 5));
-          const bool was = valid && ((word >> lane) & 1u);
-          bool keep = was, amb = false;
-          if (was) {
+        GSYNC();
+        // (C2) exact refinement of the candidates for the maximum
+        {
+          const float mlo = __uint_as_float(vload(ctl->mlo_bits));
+          for (int j = f0 + warp; j < f1; j += nwarps) {
+            const bool in = a.xtr_scope == 0 || ((__ldcg(WS(uint32_t, mask) + (j >> 5)) >> (j & 31)) & 1u);
+            if (!in) continue;
             const float c = __ldcg(WS(float, ctil) + j);
             const float nf = __ldcg(WS(float, nrmf) + j);
             float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
-            float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
-            float nfr = nf;  // ||x~_j|| rounded up: the radius term's norm
-            if constexpr (EN) {
-              E = __fadd_ru(E, ridge_err(j, c));
-              nfr = __fsqrt_ru(__fadd_ru(__fmul_ru(nf, nf), __double2float_ru(rdg)));
-              nfl = __fsqrt_rd(__fadd_rd(__fmul_rd(nfl, nfl), __double2float_rd(rdg)));
+            if constexpr (EN) E = __fadd_ru(E, ridge_err(j, c));
+            if (__fadd_ru(fabsf(c), E) >= mlo) {
+              const df2 ce = warp_dot_exact<NG, XLO>(cx, j, WS(float, rho_h), WS(float, rho_l), __fmul_ru(nf, rnormf));
+              double cv = df_to_double(ce);
+              if constexpr (EN) cv = __dsub_rn(cv, ridge_exact(j));
+              cv = fabs(cv);
+              if (lane == 0) atomicMax(&ctl->m_bits, (unsigned long long)__double_as_longlong(cv));
             }
-            // rigorous FP32 brackets of mu_j = |c_j| |alpha| + r ||x_j||
-            const float mu_hi = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(c), E), aaf_hi), __fmul_ru(radf_hi, nfr));
-            const float clo = fmaxf(__fsub_rd(fabsf(c), E), 0.f);
-            const float mu_lo = __fadd_rd(__fmul_rd(clo, aaf_lo), __fmul_rd(radf_lo, nfl));
-            // a feature the sphere screens for certain is screened by the
-            // dome too (the dome lies inside the sphere); any other one gets
-            // the exact evaluation when the dome runs
-            if (mu_hi < 0.999999f) keep = false;
-            else if (mu_lo >= 1.000001f && !dome) keep = true;
-            else amb = true;
           }
-          // exact decision for the undecided ones, as the FP64 tests of
-          // Eq. (7) (sphere) and Eq. (11) (dome)
-          unsigned ambm = __ballot_sync(0xffffffffu, amb);
-          while (ambm) {
-            const int l = __ffs(ambm) - 1;
-            ambm &= ambm - 1;
-            const int jj = w0 + l;
-            const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldcg(WS(float, nrmf) + jj), rnormf));
-            double cj = df_to_double(ce), xn = __ldcg(WS(double, nrm) + jj);
-            if constexpr (EN) {
-              cj = __dsub_rn(cj, ridge_exact(jj));
-              xn = __dsqrt_rn(__dadd_rn(__dmul_rn(xn, xn), rdg));
-            }
-            const double mu = __dadd_rn(__dmul_rn(fabs(cj), aa), __dmul_rn(rad, xn));
-            bool kp = !(mu < 1.0);
-            if (dome) {
-              const double xt = __dmul_rn(alpha, cj);                       // x_j^T theta
-              const double xy = __ddiv_rn(__ldcg(WS(double, cy) + jj), lam);  // x_j^T y / lambda
-              const double xc = __dmul_rn(0.5, __dadd_rn(xy, xt));          // x_j^T center
-              const double xnr = __ddiv_rn(__dsub_rn(xy, xt), dR);          // x_j^T normal
-              const double md = fmax(dome_support(xc, drad, dal, xnr, xn), dome_support(-xc, drad, dal, -xnr, xn));
-              if (md < 1.0) kp = false;
-            }
-            if (lane == l) keep = kp;
-          }
-          const float2 bj = valid ? ld_beta(cx, j) : make_float2(0.f, 0.f);
-          bool nz = nonzero2(bj);
-          // a newly screened nonzero coefficient is set to zero when the
-          // solver goes on (Remark 3); its residual share is added back by CTA 0
-          const bool zeroed = was && !keep && nz && !stop && !cap;
-          if (zeroed) {
-            WS(double, zl_b)[j] = __dadd_rn((double)bj.x, (double)bj.y);
-            WS(float2, bdf)[j] = make_float2(0.f, 0.f);
-            nz = false;
-          }
-          const uint32_t zw = __ballot_sync(0xffffffffu, zeroed);
-          zero += __popc(zw);
-          const uint32_t nwd = __ballot_sync(0xffffffffu, keep);
-          if (lane == 0) {
-            WS(uint32_t, mask)[w0 >> 5] = nwd;
-            WS(uint32_t, zbits)[w0 >> 5] = zw;
-          }
-          kept += __popc(nwd);
-          sup += __popc(__ballot_sync(0xffffffffu, keep && nz));
-          nnz += __popc(__ballot_sync(0xffffffffu, valid && nz));
-        }
-        if (lane != 0) kept = sup = nnz = zero = 0;
-        kept = block_sum_i(kept, ibuf);
-        sup = block_sum_i(sup, ibuf);
-        nnz = block_sum_i(nnz, ibuf);
-        zero = block_sum_i(zero, ibuf);
-        if (tid == 0) {
-          WS(int, cnt_kept)[cta] = kept;
-          WS(int, cnt_sup)[cta] = sup;
-          WS(int, cnt_nnz)[cta] = nnz;
-          WS(int, cnt_zero)[cta] = zero;
-        }
-      }
-      GSYNC();
-      // (C4) totals and this CTA's offsets; the maxima are reset for the next check
-      int totk = 0, tots = 0, totn = 0, totz = 0, pk = 0, ps = 0, pz = 0;
-      for (int c = tid; c < G; c += kThreads) {
-        const int k = __ldcg(WS(int, cnt_kept) + c), s = __ldcg(WS(int, cnt_sup) + c), z = __ldcg(WS(int, cnt_zero) + c);
-        totk += k;
-        tots += s;
-        totz += z;
-        totn += __ldcg(WS(int, cnt_nnz) + c);
-        if (c < cta) {
-          pk += k;
-          ps += s;
-          pz += z;
-        }
-      }
-      totk = block_sum_i(totk, ibuf);
-      tots = block_sum_i(tots, ibuf);
-      totn = block_sum_i(totn, ibuf);
-      totz = block_sum_i(totz, ibuf);
-      pk = block_sum_i(pk, ibuf);
-      ps = block_sum_i(ps, ibuf);
-      pz = block_sum_i(pz, ibuf);
-      if (cta == 0 && tid == 0) {
-        ctl->m_bits = 0ull;
-        ctl->mlo_bits = 0u;
-      }
-      if (stop || cap) {
-        // outputs of this lambda
-        for (int j = f0 + tid; j < f1; j += kThreads) {
-          const float2 b = ld_beta(cx, j);
-          bout[(long long)t * a.p + j] = __dadd_rn((double)b.x, (double)b.y);
-        }
-        if (mout)
-          for (int w = wd0 + tid; w < wd1; w += kThreads)
-            mout[(long long)t * a.words + w] = __ldcg(WS(uint32_t, mask) + w);
-        if (cta == 0 && tid == 0) {
-          lasso_path_stats st;
-          st.lambda = lam_path;
-          st.primal = P;
-          st.dual = D;
-          st.gap = Gap;
-          st.radius = rad;
-          st.alpha = alpha;
-          st.epochs = epochs;
-          st.checks = checks;
-          st.n_active = totk;
-          st.n_nonzero = totn;
-          st.x_columns = xcols;
-          st.converged = stop ? 1 : 0;
-          st.status = stop ? kStatusOK : kStatusNotConverged;
-          st.bound_ratio = __longlong_as_double((long long)vload(ctl->aud_bits));
-          st.bound_ratio_tc = __longlong_as_double((long long)vload(ctl->aud_tc_bits));
-          ctl->aud_bits = 0ull;
-          ctl->aud_tc_bits = 0ull;
-          sout[t] = st;
         }
         GSYNC();
-        break;
-      }
-      // compaction: ascending safe-active list A, support positions sup0 and
-      // the ascending list of coefficients the check set to zero.  Each warp
-      // takes a contiguous run of the slice's mask words: count, prefix over
-      // the warps, write.
-      {
-        const int w_first = wd0, w_last = wd1;
-        const int nwd = w_last - w_first, per = (nwd + nwarps - 1) / nwarps;
-        const int wb = w_first + warp * per, we = min(w_last, wb + per);
-        int ck = 0, cs_ = 0, cz = 0;
-        for (int w = wb; w < we; ++w) {
-          const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
-          const int j = w * 32 + lane;
-          const bool keep = (word >> lane) & 1u;
-          const bool nz = keep && nonzero2(ld_beta(cx, j));
-          ck += __popc(word);
-          cs_ += __popc(__ballot_sync(0xffffffffu, nz));
-          cz += __popc(__ldcg(WS(uint32_t, zbits) + w));
+        // (C3) objectives, gap, radius (identical in every CTA); sphere test on the slice
+        double l1 = 0.0;
+        for (int c = tid; c < G; c += kThreads) l1 = __dadd_rn(l1, __ldcg(WS(double, part_l1) + c));
+        l1 = block_sum_d(l1, dbuf);
+        double l2 = 0.0;
+        if constexpr (EN) {
+          // ||rho~||^2 = ||rho||^2 + mu ||beta||^2
+          for (int c = tid; c < G; c += kThreads) l2 = __dadd_rn(l2, __ldcg(WS(double, part_l2) + c));
+          l2 = block_sum_d(l2, dbuf);
+          rr = __dadd_rn(rr, __dmul_rn(rdg, l2));
         }
-        __syncthreads();
-        if (lane == 0) {
-          ibuf[warp] = ck;
-          ibuf[8 + warp] = cs_;
-          ibuf[16 + warp] = cz;
-        }
-        __syncthreads();
-        int runk = pk, runs = ps, runz = pz;
-        for (int w = 0; w < warp; ++w) {
-          runk += ibuf[w];
-          runs += ibuf[8 + w];
-          runz += ibuf[16 + w];
-        }
-        __syncthreads();
-        const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
-        for (int w = wb; w < we; ++w) {
-          const int j = w * 32 + lane;
-          const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
-          const uint32_t zw = __ldcg(WS(uint32_t, zbits) + w);
-          const bool keep = (word >> lane) & 1u;
-          const bool nz = keep && nonzero2(ld_beta(cx, j));
-          const unsigned lower = (1u << lane) - 1u;
-          const int kpos = runk + __popc(word & lower);
-          const unsigned smk = __ballot_sync(0xffffffffu, nz);
-          if (keep) {
-            // certificate of a zero coefficient: slack / ||x_j|| with
-            // slack <= lambda - |x_j^T rho| (the check's c~ and its bound);
-            // nonzero coefficients are chain entries (never verified)
-            float sk = kSkChain;
-            if (!nz) {
-              const float nf = __ldcg(WS(float, nrmf) + j);
-              const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
-              const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(__ldcg(WS(float, ctil) + j)), E));
-              sk = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
-            }
-            WS(float, sk)[kpos] = sk;
-            WS(float, mref)[kpos] = 0.f;
-            WS(int, A)[kpos] = j;
+        const double m = __longlong_as_double((long long)vload(ctl->m_bits));
+        double alpha;
+        if (a.dual_point == 0) {
+          alpha = __drcp_rn(lam > m ? lam : m);
+        } else if (rr == 0.0) {
+          alpha = 0.0;
+        } else {
+          double al = __ddiv_rn(yr, __dmul_rn(lam, rr));
+          if (m > 0.0) {
+            const double lim = __drcp_rn(m);
+            if (al < -lim) al = -lim;
+            if (al > lim) al = lim;
           }
-          if (nz) WS(int, sup0)[runs + __popc(smk & lower)] = kpos;
-          if ((zw >> lane) & 1u) WS(int, zl_j)[runz + __popc(zw & lower)] = j;
-          runk += __popc(word);
-          runs += __popc(smk);
-          runz += __popc(zw);
+          alpha = al;
         }
+        double d2 = 0.0;
+        for (int i = tid; i < a.n; i += kThreads) {
+          const double r = __dadd_rn((double)__ldcg(WS(float, rho_h) + i), (double)__ldcg(WS(float, rho_l) + i));
+          const double dd = __dsub_rn(__dmul_rn(lam, __dmul_rn(alpha, r)), yv[i]);
+          d2 = __fma_rn(dd, dd, d2);
+        }
+        d2 = block_sum_d(d2, dbuf);
+        if constexpr (EN) {
+          // the augmented rows: (lambda alpha (-sqrt(mu) beta_j))^2
+          const double la = __dmul_rn(lam, alpha);
+          d2 = __dadd_rn(d2, __dmul_rn(__dmul_rn(la, la), __dmul_rn(rdg, l2)));
+        }
+        const double yy = vload(ctl->yy);
+        const double P = __dadd_rn(__dmul_rn(0.5, rr), __dmul_rn(lam, l1));
+        const double D = __dsub_rn(__dmul_rn(0.5, yy), __dmul_rn(0.5, d2));
+        const double Gap = __dsub_rn(P, D);
+        const double tau = 2.0 * (double)(a.n + a.p + (EN ? a.p : 0) + 8) * u64 * (rr + lam * l1 + yy + d2);
+        const double Gs = (Gap > 0.0 ? Gap : 0.0) + tau;
+        double rad = __ddiv_rn(__dsqrt_rn(__dmul_rn(2.0, Gs)), lam);
+        if (a.refined_radius == 1) {
+          // Thm. 2's radius (R^2 - r(beta)^2)^(1/2): sqrt(2 G)/lambda, or R =
+          // ||theta - y/lambda|| when the clipped r(beta) is 0 (P > ||y||^2/2)
+          const double Rt = __ddiv_rn(__dsqrt_rn(__dadd_rn(d2, tau)), lam);
+          if (Rt < rad) rad = Rt;
+        }
+        const double aa = fabs(alpha);
+        // GAP SAFE dome (Eq. (11), parameters of the appendix): center
+        // (y/lambda + theta)/2, radius R/2 with R = ||y/lambda - theta||, unit
+        // normal (y/lambda - theta)/R, ratio 2 r^2/R^2 - 1 with r the radius of
+        // Thm. 2 from the primal point; lambda^2 R^2 is enlarged and lambda^2 r^2
+        // reduced by the rounding bound tau, as the sphere's gap is.  When
+        // theta = y/lambda the dome is a point and only the sphere runs.
+        const bool dome = a.screen_rule == 1 && d2 > 0.0;
+        double drad = 0.0, dal = 0.0, dR = 1.0;
+        if (dome) {
+          const double big = __dadd_rn(d2, tau);
+          double small = __dsub_rn(__dsub_rn(yy, __dmul_rn(2.0, P)), tau);
+          if (small < 0.0) small = 0.0;
+          double q = __ddiv_rn(small, big);
+          if (q > 1.0) q = 1.0;
+          dal = __dsub_rn(__dmul_rn(2.0, q), 1.0);
+          drad = __ddiv_rn(__dmul_rn(0.5, __dsqrt_rn(big)), lam);
+          dR = __ddiv_rn(__dsqrt_rn(d2), lam);
+        }
+        ++checks;
+        xcols += scope_n;
+        const bool stop = Gap <= vload(ctl->eps);
+        const bool cap = epochs >= a.max_epochs;
+        {
+          const float aaf_lo = __double2float_rd(aa), aaf_hi = __double2float_ru(aa);
+          const float radf_lo = __double2float_rd(rad), radf_hi = __double2float_ru(rad);
+          int kept = 0, sup = 0, nnz = 0, zero = 0;
+          // each warp handles 32 consecutive features = one mask word
+          for (int w0 = f0 + 32 * warp; w0 < f1; w0 += 32 * nwarps) {
+            const int j = w0 + lane;
+            const bool valid = j < f1;
+            const uint32_t word = __ldcg(WS(uint32_t, mask) + (w0 >> 5));
+            const bool was = valid && ((word >> lane) & 1u);
+            bool keep = was, amb = false;
+            if (was) {
+              const float c = __ldcg(WS(float, ctil) + j);
+              const float nf = __ldcg(WS(float, nrmf) + j);
+              float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+              float nfl = __double2float_rd(__ldcg(WS(double, nrm) + j));
+              float nfr = nf;  // ||x~_j|| rounded up: the radius term's norm
+              if constexpr (EN) {
+                E = __fadd_ru(E, ridge_err(j, c));
+                nfr = __fsqrt_ru(__fadd_ru(__fmul_ru(nf, nf), __double2float_ru(rdg)));
+                nfl = __fsqrt_rd(__fadd_rd(__fmul_rd(nfl, nfl), __double2float_rd(rdg)));
+              }
+              // rigorous FP32 brackets of mu_j = |c_j| |alpha| + r ||x_j||
+              const float mu_hi = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(c), E), aaf_hi), __fmul_ru(radf_hi, nfr));
+              const float clo = fmaxf(__fsub_rd(fabsf(c), E), 0.f);
+              const float mu_lo = __fadd_rd(__fmul_rd(clo, aaf_lo), __fmul_rd(radf_lo, nfl));
+              // a feature the sphere screens for certain is screened by the
+              // dome too (the dome lies inside the sphere); any other one gets
+              // the exact evaluation when the dome runs
+              if (mu_hi < 0.999999f) keep = false;
+              else if (mu_lo >= 1.000001f && !dome) keep = true;
+              else amb = true;
+            }
+            // exact decision for the undecided ones, as the FP64 tests of
+            // Eq. (7) (sphere) and Eq. (11) (dome)
+            unsigned ambm = __ballot_sync(0xffffffffu, amb);
+            while (ambm) {
+              const int l = __ffs(ambm) - 1;
+              ambm &= ambm - 1;
+              const int jj = w0 + l;
+              const df2 ce = warp_dot_exact<NG, XLO>(cx, jj, WS(float, rho_h), WS(float, rho_l), __fmul_ru(__ldcg(WS(float, nrmf) + jj), rnormf));
+              double cj = df_to_double(ce), xn = __ldcg(WS(double, nrm) + jj);
+              if constexpr (EN) {
+                cj = __dsub_rn(cj, ridge_exact(jj));
+                xn = __dsqrt_rn(__dadd_rn(__dmul_rn(xn, xn), rdg));
+              }
+              const double mu = __dadd_rn(__dmul_rn(fabs(cj), aa), __dmul_rn(rad, xn));
+              bool kp = !(mu < 1.0);
+              if (dome) {
+                const double xt = __dmul_rn(alpha, cj);                       // x_j^T theta
+                const double xy = __ddiv_rn(__ldcg(WS(double, cy) + jj), lam);  // x_j^T y / lambda
+                const double xc = __dmul_rn(0.5, __dadd_rn(xy, xt));          // x_j^T center
+                const double xnr = __ddiv_rn(__dsub_rn(xy, xt), dR);          // x_j^T normal
+                const double md = fmax(dome_support(xc, drad, dal, xnr, xn), dome_support(-xc, drad, dal, -xnr, xn));
+                if (md < 1.0) kp = false;
+              }
+              if (lane == l) keep = kp;
+            }
+            const float2 bj = valid ? ld_beta(cx, j) : make_float2(0.f, 0.f);
+            bool nz = nonzero2(bj);
+            // a newly screened nonzero coefficient is set to zero when the
+            // solver goes on (Remark 3); its residual share is added back by CTA 0
+            const bool zeroed = was && !keep && nz && !stop && !cap;
+            if (zeroed) {
+              WS(double, zl_b)[j] = __dadd_rn((double)bj.x, (double)bj.y);
+              WS(float2, bdf)[j] = make_float2(0.f, 0.f);
+              nz = false;
+            }
+            const uint32_t zw = __ballot_sync(0xffffffffu, zeroed);
+            zero += __popc(zw);
+            const uint32_t nwd = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) {
+              WS(uint32_t, mask)[w0 >> 5] = nwd;
+              WS(uint32_t, zbits)[w0 >> 5] = zw;
+            }
+            kept += __popc(nwd);
+            sup += __popc(__ballot_sync(0xffffffffu, keep && nz));
+            nnz += __popc(__ballot_sync(0xffffffffu, valid && nz));
+          }
+          if (lane != 0) kept = sup = nnz = zero = 0;
+          kept = block_sum_i(kept, ibuf);
+          sup = block_sum_i(sup, ibuf);
+          nnz = block_sum_i(nnz, ibuf);
+          zero = block_sum_i(zero, ibuf);
+          if (tid == 0) {
+            WS(int, cnt_kept)[cta] = kept;
+            WS(int, cnt_sup)[cta] = sup;
+            WS(int, cnt_nnz)[cta] = nnz;
+            WS(int, cnt_zero)[cta] = zero;
+          }
+        }
+        GSYNC();
+        // (C4) totals and this CTA's offsets; the maxima are reset for the next check
+        int totk = 0, tots = 0, totn = 0, totz = 0, pk = 0, ps = 0, pz = 0;
+        for (int c = tid; c < G; c += kThreads) {
+          const int k = __ldcg(WS(int, cnt_kept) + c), s = __ldcg(WS(int, cnt_sup) + c), z = __ldcg(WS(int, cnt_zero) + c);
+          totk += k;
+          tots += s;
+          totz += z;
+          totn += __ldcg(WS(int, cnt_nnz) + c);
+          if (c < cta) {
+            pk += k;
+            ps += s;
+            pz += z;
+          }
+        }
+        totk = block_sum_i(totk, ibuf);
+        tots = block_sum_i(tots, ibuf);
+        totn = block_sum_i(totn, ibuf);
+        totz = block_sum_i(totz, ibuf);
+        pk = block_sum_i(pk, ibuf);
+        ps = block_sum_i(ps, ibuf);
+        pz = block_sum_i(pz, ibuf);
+        if (cta == 0 && tid == 0) {
+          ctl->m_bits = 0ull;
+          ctl->mlo_bits = 0u;
+        }
+        if (stop || cap) {
+          // outputs of this lambda
+          for (int j = f0 + tid; j < f1; j += kThreads) {
+            const float2 b = ld_beta(cx, j);
+            bout[(long long)t * a.p + j] = __dadd_rn((double)b.x, (double)b.y);
+          }
+          if (mout)
+            for (int w = wd0 + tid; w < wd1; w += kThreads)
+              mout[(long long)t * a.words + w] = __ldcg(WS(uint32_t, mask) + w);
+          if (cta == 0 && tid == 0) {
+            lasso_path_stats st;
+            st.lambda = lam_path;
+            st.primal = P;
+            st.dual = D;
+            st.gap = Gap;
+            st.radius = rad;
+            st.alpha = alpha;
+            st.epochs = epochs;
+            st.checks = checks;
+            st.n_active = totk;
+            st.n_nonzero = totn;
+            st.x_columns = xcols;
+            st.converged = stop ? 1 : 0;
+            st.status = stop ? kStatusOK : kStatusNotConverged;
+            st.bound_ratio = __longlong_as_double((long long)vload(ctl->aud_bits));
+            st.bound_ratio_tc = __longlong_as_double((long long)vload(ctl->aud_tc_bits));
+            ctl->aud_bits = 0ull;
+            ctl->aud_tc_bits = 0ull;
+            sout[t] = st;
+          }
+          GSYNC();
+          break;
+        }
+        // compaction: ascending safe-active list A, support positions sup0 and
+        // the ascending list of coefficients the check set to zero.  Each warp
+        // takes a contiguous run of the slice's mask words: count, prefix over
+        // the warps, write.
+        {
+          const int w_first = wd0, w_last = wd1;
+          const int nwd = w_last - w_first, per = (nwd + nwarps - 1) / nwarps;
+          const int wb = w_first + warp * per, we = min(w_last, wb + per);
+          int ck = 0, cs_ = 0, cz = 0;
+          for (int w = wb; w < we; ++w) {
+            const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
+            const int j = w * 32 + lane;
+            const bool keep = (word >> lane) & 1u;
+            const bool nz = keep && nonzero2(ld_beta(cx, j));
+            ck += __popc(word);
+            cs_ += __popc(__ballot_sync(0xffffffffu, nz));
+            cz += __popc(__ldcg(WS(uint32_t, zbits) + w));
+          }
+          __syncthreads();
+          if (lane == 0) {
+            ibuf[warp] = ck;
+            ibuf[8 + warp] = cs_;
+            ibuf[16 + warp] = cz;
+          }
+          __syncthreads();
+          int runk = pk, runs = ps, runz = pz;
+          for (int w = 0; w < warp; ++w) {
+            runk += ibuf[w];
+            runs += ibuf[8 + w];
+            runz += ibuf[16 + w];
+          }
+          __syncthreads();
+          const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
+          for (int w = wb; w < we; ++w) {
+            const int j = w * 32 + lane;
+            const uint32_t word = __ldcg(WS(uint32_t, mask) + w);
+            const uint32_t zw = __ldcg(WS(uint32_t, zbits) + w);
+            const bool keep = (word >> lane) & 1u;
+            const bool nz = keep && nonzero2(ld_beta(cx, j));
+            const unsigned lower = (1u << lane) - 1u;
+            const int kpos = runk + __popc(word & lower);
+            const unsigned smk = __ballot_sync(0xffffffffu, nz);
+            if (keep) {
+              // certificate of a zero coefficient: slack / ||x_j|| with
+              // slack <= lambda - |x_j^T rho| (the check's c~ and its bound);
+              // nonzero coefficients are chain entries (never verified)
+              float sk = kSkChain;
+              if (!nz) {
+                const float nf = __ldcg(WS(float, nrmf) + j);
+                const float E = __fmul_ru(__fmul_ru(bfc, nf), rnormf) + 1e-37f;
+                const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(__ldcg(WS(float, ctil) + j)), E));
+                sk = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
+              }
+              WS(float, sk)[kpos] = sk;
+              WS(float, mref)[kpos] = 0.f;
+              WS(float, dref)[kpos] = 0.f;
+              WS(int, A)[kpos] = j;
+            }
+            if (nz) WS(int, sup0)[runs + __popc(smk & lower)] = kpos;
+            if ((zw >> lane) & 1u) WS(int, zl_j)[runz + __popc(zw & lower)] = j;
+            runk += __popc(word);
+            runs += __popc(smk);
+            runz += __popc(zw);
+          }
+        }
+        if (cta == 0 && tid == 0) {
+          ctl->q = totk;
+          ctl->s = tots;
+          ctl->nzl = totz;
+          ctl->mcur = 0.f;
+          ctl->win = totk;
+          ctl->anorm = rnormf;
+        }
+        // the anchor of the distance bound: the residual of this check
+        if (!SP)
+          for (int i = tid; i < a.ldw; i += kThreads) WS(float, anchor)[i] = __ldcg(WS(float, rho_h) + i);
+        scope_n = a.xtr_scope == 0 ? a.p : totk;
+        GSYNC();
+        PROF(0);
+      } else {
+        // (P0) pass mode, a resumed lambda: the certificates of the zero
+        // coefficients are issued anew from the product's c~ of the residual
+        // this pass starts from (the rule of the check's certificates, with
+        // the product's error factor), and the movement bound restarts at 0.
+        // Without a product the certificates of the last pass stand.
+        PROF(7);
+        if (cvalid) {
+          double rr = 0.0;
+          for (int i = tid; i < a.n; i += kThreads) {
+            const double r = __dadd_rn((double)__ldcg(WS(float, rho_h) + i), (double)__ldcg(WS(float, rho_l) + i));
+            rr = __fma_rn(r, r, rr);
+          }
+          rr = block_sum_d(rr, dbuf);
+          const float rnormf = __fmul_ru(__fsqrt_ru(__double2float_ru(rr)), 1.0001f);
+          const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
+          const int q = vload(ctl->q);
+          // four positions per thread and step, their loads issued together
+          for (int k0 = tid; k0 < q; k0 += 4 * kThreads) {
+            int jj[4];
+            float2 bb[4];
+            float nn[4], cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = k0 + u * kThreads;
+              jj[u] = k < q ? __ldcg(WS(int, A) + k) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              bb[u] = ld_beta(cx, jj[u]);
+              nn[u] = __ldcg(WS(float, nrmf) + jj[u]);
+              cc[u] = __ldcg(a.cfirst + (size_t)jj[u] + (size_t)b * a.ldc);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int k = k0 + u * kThreads;
+              if (k >= q) break;
+              float sk = kSkChain;
+              if (!nonzero2(bb[u])) {
+                const float E = __fmul_ru(__fmul_ru(a.cfactor, nn[u]), rnormf) + 1e-37f;
+                const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(cc[u]), E));
+                sk = (slack > 0.f && nn[u] > 0.f) ? __fdiv_rd(slack, nn[u]) : kSkNone;
+              }
+              WS(float, sk)[k] = sk;
+              WS(float, mref)[k] = 0.f;
+              WS(float, dref)[k] = 0.f;
+            }
+          }
+          for (int i = tid; i < a.ldw; i += kThreads) WS(float, anchor)[i] = __ldcg(WS(float, rho_h) + i);
+          __syncthreads();
+          if (tid == 0) {
+            ctl->mcur = 0.f;
+            ctl->anorm = rnormf;
+          }
+        }
+        GSYNC();
+        PROF(0);
       }
-      if (cta == 0 && tid == 0) {
-        ctl->q = totk;
-        ctl->s = tots;
-        ctl->nzl = totz;
-        ctl->mcur = 0.f;
-        ctl->win = totk;
-      }
-      scope_n = a.xtr_scope == 0 ? a.p : totk;
-      GSYNC();
-      PROF(0);
       // ======================= PASSES =======================
       {
         const int q = vload(ctl->q);
         int s = vload(ctl->s);
-        int* sup = WS(int, sup0);
-        int* sup_next = WS(int, sup1);
+        // a check's compaction writes sup0; a resumed pass continues with the list in use
+        const bool par = skip_check && vload(ctl->sup_par) != 0;
+        int* sup = par ? WS(int, sup1) : WS(int, sup0);
+        int* sup_next = par ? WS(int, sup0) : WS(int, sup1);
         // Planning of a round (single path, CTA 0): the chain = [forced
         // entry] + the support positions of the window [pos, pos + win) (at
         // most s_cap of them).  The round ends at the window's end, or at the
@@ -1531,7 +1646,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           }
           GSYNC();
         }
-        for (int e = 0; e < a.f && epochs < a.max_epochs; ++e) {
+        for (int e = e_first; e < a.f && epochs < a.max_epochs; ++e) {
           // ---- one pass over the safe-active list, in rounds
           if (!SP && cta == 0) {
             load_rho_regs<NGC, CW>(cx, WS(float, rho_h), WS(float, rho_l), rh, rl);
@@ -1632,100 +1747,188 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               const int gw = cta * nwarps + warp, nwg = G * nwarps;
               const int chunk = (span + nwg - 1) / nwg;
               const int i0 = pos + gw * chunk, i1 = min(rend, i0 + chunk);
+              // one-CTA problems: D_c = ||rho_c - rho_a||, an upper bound of the
+              // distance of snapshot c of the round from the anchor rho_a, and
+              // their maximum.  FP32 over the high planes: the sum of squares is
+              // enlarged by its accumulation error ((terms per lane + 8) 2^-23),
+              // and 2^-22 (||rho_c|| + ||rho_a||) covers the dropped low planes
+              // (each below 2^-24 of its high plane) and the differences' rounding
+              float dmax = 3.0e38f;
+              const long long td0 = clock64();
+              if (!SP) {
+                const float4* anc = reinterpret_cast<const float4*>(WS(float, anchor));
+                const float abs_t = __fmul_ru(2.384185791015625e-07f, __fadd_ru(rb, vload(ctl->anorm)));
+                const float fac = __fadd_ru(1.0f, __fmul_ru((float)(4 * ((a.ld4 + 31) / 32) + 8), 1.1920929e-07f));
+                for (int c = warp; c <= nc; c += nwarps) {
+                  const float4* sh = reinterpret_cast<const float4*>(WS(float, snap) + (size_t)c * 2 * a.ldw);
+                  float S = 0.f;
+                  for (int g = lane; g < a.ld4; g += 32) {
+                    const float4 x = __ldcg(sh + g), y = __ldcg(anc + g);
+                    const float d0 = __fsub_rn(x.x, y.x), d1 = __fsub_rn(x.y, y.y);
+                    const float d2 = __fsub_rn(x.z, y.z), d3 = __fsub_rn(x.w, y.w);
+                    S = __fmaf_rn(d0, d0, S);
+                    S = __fmaf_rn(d1, d1, S);
+                    S = __fmaf_rn(d2, d2, S);
+                    S = __fmaf_rn(d3, d3, S);
+                  }
+                  S = warp_sum_f(S);
+                  if (lane == 0)
+                    WS(float, dsnap)[c] = __fadd_ru(__fmul_ru(__fsqrt_ru(__fmul_ru(S, fac)), 1.0001f), abs_t);
+                }
+                __syncthreads();
+                float m = 0.f;
+                for (int c = lane; c <= nc; c += 32) m = fmaxf(m, __ldcg(WS(float, dsnap) + c));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                dmax = m;
+                if (tid == 0) {
+                  ctl->gprof[0] += 1ull;
+                  ctl->gprof[4] += (unsigned long long)(clock64() - td0);
+                }
+              }
+              unsigned long long n_scan = 0, n_read = 0, n_exact = 0;
               if (span > 0 && i0 < i1) {
                 // a zero coefficient whose certificate survives the movement of
                 // the residual since it was issued stays zero without a read:
-                // |x_j^T rho| <= lambda - slack + ||x_j|| (M_now - M_ref) < lambda
+                // |x_j^T rho| <= lambda - slack + ||x_j|| ||rho - rho_ref|| < lambda,
+                // with ||rho - rho_ref|| <= M_now - M_ref (the movement counter)
+                // and, for one-CTA problems, <= D_max + D_ref (both distances
+                // from the anchor, the triangle inequality)
                 const float mend = __ldcg(WS(float, msnap) + nc);
                 const float* skp = WS(float, sk);
                 float* mrp = WS(float, mref);
-                int seg = lower_bound_i(WS(int, chain), nc, i0);
+                // chain entries before the current batch of positions
+                int sb = lower_bound_i(WS(int, chain), nc, i0);
                 float4 r4[NG];
                 int loaded = -1;
                 const float lamf = __double2float_rn(lam);
                 const float lam_lo = __fmul_rd(__double2float_rd(lam), 1.0f - 1e-6f);
+                // the verdict for position i (feature j, norm nf) from its FP32
+                // correlation c with snapshot sg: stays zero (certificate
+                // renewed) or enters
+                auto decide = [&](int i, int j, float nf, float c, int sg) -> bool {
+                  const float* sh = WS(float, snap) + (size_t)sg * 2 * a.ldw;
+                  const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
+                  bool enters;
+                  if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
+                  else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
+                  else {
+                    ++n_exact;
+                    const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
+                    df2 nb, d;
+                    cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
+                    enters = !df_is_zero(d);
+                  }
+                  if (enters) {
+                    if (lane == 0) atomicMin(&ctl->fstar, i);
+                  } else if (lane == 0) {
+                    const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
+                    WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
+                    mrp[i] = __ldcg(WS(float, msnap) + sg);
+                    if (!SP) WS(float, dref)[i] = __ldcg(WS(float, dsnap) + sg);
+                  }
+                  return enters;
+                };
                 bool stop_warp = false;
                 for (int base = i0; base < i1 && !stop_warp; base += 32) {
                   const int il = base + lane;
+                  n_scan += 32;
+                  // the certificate test, with the feature of the position read
+                  // alongside (used when the test fails)
                   bool need = false;
+                  int jn = 0;
                   if (il < i1) {
                     const float sk = __ldcg(skp + il);
-                    need = !(__fsub_ru(mend, __ldcg(mrp + il)) < sk);
+                    const float mr = __ldcg(mrp + il);
+                    const float dr = SP ? 0.f : __ldcg(WS(float, dref) + il);
+                    jn = __ldcg(WS(int, A) + il);
+                    float mv = __fsub_ru(mend, mr);
+                    if (!SP) mv = fminf(mv, __fadd_ru(dmax, dr));
+                    need = !(mv < sk);
                   }
                   unsigned needm = __ballot_sync(0xffffffffu, need);
-                  // the verdict for position i from its FP32 correlation c with the
-                  // snapshot sh: stays zero (certificate renewed) or enters
-                  auto decide = [&](int i, int j, float c, const float* sh) -> bool {
-                    const float nf = __ldcg(WS(float, nrmf) + j);
-                    const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
-                    bool enters;
-                    if (__fadd_ru(fabsf(c), E) < lamf * (1.0f - 1e-6f)) enters = false;
-                    else if (__fsub_rd(fabsf(c), E) > lamf * (1.0f + 1e-6f)) enters = true;
-                    else {
-                      const df2 g = warp_dot_exact<NG, XLO>(cx, j, sh, sh + a.ldw, __fmul_ru(nf, rb));
-                      df2 nb, d;
-                      cd_update(g, df2{0.f, 0.f}, __ldcg(WS(float4, ftab) + j), nb, d);
-                      enters = !df_is_zero(d);
-                    }
-                    if (enters) {
-                      if (lane == 0) atomicMin(&ctl->fstar, i);
-                    } else if (lane == 0) {
-                      const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
-                      WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
-                      mrp[i] = __ldcg(WS(float, msnap) + seg);
-                    }
-                    return enters;
-                  };
+                  if (needm == 0u) continue;
+                  // fstar moves under other warps' atomicMin: one lane reads it
+                  // so that the whole warp takes the same branches.  A value
+                  // that is stale by the end of the batch only costs work: a
+                  // verdict past the first entering position is undone with
+                  // the round, and the certificates it renews stay valid
+                  const int fs = __shfl_sync(0xffffffffu, vload(ctl->fstar), 0);
+                  if (base + __ffs(needm) - 1 > fs) break;
+                  const float nfn = need ? __ldcg(WS(float, nrmf) + jn) : 0.f;
+                  // the snapshot of each lane's position: the chain entries
+                  // before it, sb (entries before base) plus those of the
+                  // batch below it (a search over the ascending entries held
+                  // one per lane; at most 31 of them lie in the batch)
+                  for (;;) {
+                    const int ce = (sb + lane < nc) ? __ldcg(WS(int, chain) + sb + lane) : 0x7fffffff;
+                    const unsigned lt = __ballot_sync(0xffffffffu, ce < base);
+                    sb += __popc(lt);
+                    if (lt != 0xffffffffu) break;
+                  }
+                  const int ce = (sb + lane < nc) ? __ldcg(WS(int, chain) + sb + lane) : 0x7fffffff;
+                  int cnt = 0;
+#pragma unroll
+                  for (int st = 16; st > 0; st >>= 1)
+                    if (__shfl_sync(0xffffffffu, ce, cnt + st - 1) < il) cnt += st;
+                  const int segl = sb + cnt;
                   while (needm) {
-                    const int i = base + __ffs(needm) - 1;
+                    const int l = __ffs(needm) - 1;
                     needm &= needm - 1;
-                    // fstar moves under other warps' atomicMin: one lane reads it
-                    // so that the whole warp takes the same branch before the
-                    // full-mask dot products below
-                    if (i > __shfl_sync(0xffffffffu, vload(ctl->fstar), 0)) {
+                    const int i = base + l;
+                    if (i > fs) {
                       stop_warp = true;
                       break;
                     }
-                    while (seg < nc && __ldcg(WS(int, chain) + seg) < i) ++seg;
-                    const float* sh = WS(float, snap) + (size_t)seg * 2 * a.ldw;
-                    if (loaded != seg) {
+                    const int j = __shfl_sync(0xffffffffu, jn, l), sg = __shfl_sync(0xffffffffu, segl, l);
+                    const float nf = __shfl_sync(0xffffffffu, nfn, l);
+                    if (loaded != sg) {
+                      const float* sh = WS(float, snap) + (size_t)sg * 2 * a.ldw;
 #pragma unroll
                       for (int k = 0; k < NG; ++k) {
                         const int g = lane + 32 * k;
                         r4[k] = (g < a.ld4) ? ldcg4(sh, g) : make_float4(0.f, 0.f, 0.f, 0.f);
                       }
-                      loaded = seg;
+                      loaded = sg;
                     }
-                    const int j = __ldcg(WS(int, A) + i);
                     // the next needed position shares the snapshot when no chain
                     // entry lies between them: verify both with one pass of loads
                     // (up to 8 granules per lane; longer columns keep one)
                     constexpr bool kPair = NG <= 8;
-                    const int seg_end = seg < nc ? __ldcg(WS(int, chain) + seg) : 0x7fffffff;
-                    const int i2 = needm ? base + __ffs(needm) - 1 : 0x7fffffff;
-                    if (kPair && i2 < seg_end) {
-                      const int j2 = __ldcg(WS(int, A) + i2);
+                    const int l2 = needm ? __ffs(needm) - 1 : 0;
+                    const int sg2 = __shfl_sync(0xffffffffu, segl, l2);
+                    if (kPair && needm && sg2 == sg && base + l2 <= fs) {
+                      const int j2 = __shfl_sync(0xffffffffu, jn, l2);
+                      const float nf2 = __shfl_sync(0xffffffffu, nfn, l2);
                       float c, c2;
+                      n_read += 2;
                       warp_dot_f32_2<NG>(a.Xh + (long long)j * a.ldx, a.Xh + (long long)j2 * a.ldx, r4, a.ld4, a.n,
                                          c, c2);
-                      if (decide(i, j, c, sh)) {
+                      if (decide(i, j, nf, c, sg)) {
                         stop_warp = true;
                         break;
                       }
                       needm &= needm - 1;
-                      if (decide(i2, j2, c2, sh)) {
+                      if (decide(base + l2, j2, nf2, c2, sg)) {
                         stop_warp = true;
                         break;
                       }
                     } else {
+                      ++n_read;
                       const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-                      if (decide(i, j, c, sh)) {
+                      if (decide(i, j, nf, c, sg)) {
                         stop_warp = true;
                         break;
                       }
                     }
                   }
                 }
+              }
+              // one-CTA problems: positions scanned, columns read, exact refinements
+              if (!SP && lane == 0) {
+                atomicAdd(&ctl->gprof[1], n_scan);
+                atomicAdd(&ctl->gprof[2], n_read);
+                atomicAdd(&ctl->gprof[3], n_exact);
               }
             }
             GSYNC();
@@ -1845,12 +2048,37 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
           int* tmp = sup;
           sup = sup_next;
           sup_next = tmp;
+          if (PM) {
+            // pass mode: the launch ends for this problem after one pass; the
+            // next launch resumes here with c~ of the new residual
+            if (tid == 0) {
+              ctl->resume = 1;
+              ctl->e_cur = e + 1;
+              ctl->ep_s = epochs;
+              ctl->ck_s = checks;
+              ctl->xc_s = xcols;
+              ctl->scope_s = scope_n;
+              ctl->sup_par = sup == WS(int, sup1) ? 1 : 0;
+            }
+            __syncthreads();
+            goto pass_exit;
+          }
         }
       }
       GSYNC();
+      skip_check = false;
+      e_first = 0;
     }
+    // the lambda is finished: a later lambda of this launch starts afresh
+    resume = false;
+    if (PM && cta == 0 && tid == 0) ctl->resume = 0;
   }  // lambda loop
+  if (PM && tid == 0) {
+    ctl->pdone = 1;
+    atomicSub(a.active, 1);
+  }
     }
+  pass_exit:
     continue;
   fail:
     // a device error on this problem (NaN/Inf input, lambda_max = 0, a wait
@@ -1865,7 +2093,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
       if (G > 1) grid_sync(bc, bg, err, (unsigned)G, a.wait_ns);
       if (cta == 0) {
         lasso_path_stats* so = a.stats + (size_t)b * a.T;
-        const int tf0 = a.lockstep ? a.t0 : 0;
+        const int tf0 = a.lockstep ? (a.pass_mode ? vload(ctl->t_cur) : a.t0) : 0;
         for (int t = tf0 + tid; t < a.T; t += kThreads) {
           lasso_path_stats st{};
           st.lambda = vload(ctl->lambda_max) * a.ratios[t];
@@ -1878,6 +2106,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
         if (tid == 0) {
           ctl->err = 0;
           ctl->failed = e;
+          if (a.lockstep && a.pass_mode) atomicSub(a.active, 1);
         }
         __syncthreads();
       }

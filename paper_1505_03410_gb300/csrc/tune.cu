@@ -4,7 +4,8 @@
 // the first check of each lambda gets X^T rho (per-CTA FP32 passes or one
 // split-BF16 tensor-core product per lambda), how many solver CTAs share an
 // SM (two, at 128 registers per thread, or one), the N tile of the
-// tensor-core product, and how many CTAs work on one problem (1, 8, 16 or
+// tensor-core product, whether a lockstep batch takes a product per lambda or
+// per coordinate pass, and how many CTAs work on one problem (1, 8, 16 or
 // 32; a group larger than the CTAs that rebuild its snapshots runs the
 // coordinate chain in Gram form, as the single path does).
 // Every candidate makes the same screening decisions (each equals the FP64
@@ -24,13 +25,13 @@ namespace lassogs {
 namespace {
 
 struct Candidate {
-  int32_t dtype, per_sm, tile_n, group;
+  int32_t dtype, per_sm, tile_n, group, pass;
 };
 
 constexpr Candidate kCandidates[] = {
-    {LASSO_F32, 2, 0, 1},    {LASSO_F32, 1, 0, 1},    {LASSO_BF16, 2, 128, 1}, {LASSO_BF16, 1, 128, 1},
-    {LASSO_BF16, 2, 256, 1}, {LASSO_BF16, 1, 256, 1}, {LASSO_F32, 2, 0, 8},    {LASSO_F32, 2, 0, 32},
-    {LASSO_F32, 1, 0, 16},
+    {LASSO_F32, 2, 0, 1, 0},    {LASSO_F32, 1, 0, 1, 0},    {LASSO_BF16, 2, 128, 1, 0}, {LASSO_BF16, 1, 128, 1, 0},
+    {LASSO_BF16, 2, 256, 1, 0}, {LASSO_BF16, 1, 256, 1, 0}, {LASSO_F32, 2, 0, 8, 0},    {LASSO_F32, 2, 0, 32, 0},
+    {LASSO_F32, 1, 0, 16, 0},   {LASSO_BF16, 2, 128, 1, 1}, {LASSO_BF16, 1, 128, 1, 1},
 };
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
@@ -51,6 +52,7 @@ TuneLayout tune_layout(int64_t n, int64_t p, int64_t sample, int32_t lambdas) {
     o.batch_ctas_per_sm = c.per_sm;
     o.gemm_tile_n = c.tile_n;
     o.batch_group = c.group;
+    o.lockstep_pass = c.pass;
     const size_t s = lasso_batch_workspace_size(n, p, sample, &o);
     if (s == 0) return t;
     a = std::max(a, s);
@@ -108,6 +110,7 @@ lasso_status lasso_batch_tune(const float* X, int64_t n, int64_t p, int64_t ldx,
     o.batch_ctas_per_sm = kCandidates[c].per_sm;
     o.gemm_tile_n = kCandidates[c].tile_n;
     o.batch_group = kCandidates[c].group;
+    o.lockstep_pass = kCandidates[c].pass;
     for (int rep = 0; rep < 2 && status == LASSO_OK; ++rep) {
       if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) status = set_error(LASSO_ERR_CUDA, "event record failed");
       if (status == LASSO_OK)
@@ -141,6 +144,7 @@ lasso_status lasso_batch_tune(const float* X, int64_t n, int64_t p, int64_t ldx,
   tuned->batch_ctas_per_sm = kCandidates[best].per_sm;
   tuned->gemm_tile_n = kCandidates[best].tile_n;
   tuned->batch_group = kCandidates[best].group;
+  tuned->lockstep_pass = kCandidates[best].pass;
   return LASSO_OK;
 }
 

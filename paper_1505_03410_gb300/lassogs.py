@@ -49,7 +49,8 @@ class LassoOpts(ctypes.Structure):
                 ("gemm_dtype", ctypes.c_int32), ("batch_ctas_per_sm", ctypes.c_int32),
                 ("gemm_tile_n", ctypes.c_int32), ("batch_group", ctypes.c_int32),
                 ("screen_rule", ctypes.c_int32), ("refined_radius", ctypes.c_int32),
-                ("enet_alpha", ctypes.c_double), ("audit_bounds", ctypes.c_int32)]
+                ("enet_alpha", ctypes.c_double), ("audit_bounds", ctypes.c_int32),
+                ("lockstep_pass", ctypes.c_int32)]
 
 
 class LassoPathStats(ctypes.Structure):

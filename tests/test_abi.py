@@ -145,7 +145,7 @@ def test_lista_host_checks(pkg):
 
 def test_tune_host_checks(pkg):
     """The autotuner's sizes and arguments are checked on the host."""
-    assert pkg.lasso_batch_tune_candidates() == 9
+    assert pkg.lasso_batch_tune_candidates() == 11
     assert pkg.lasso_batch_tune_workspace_size(100, 1000, 0, 5) == 0
     assert pkg.lasso_batch_tune_workspace_size(100, 1000, 16, 5) >= 16 * 5 * 1000 * 8
     tuned = pkg.LassoOpts()

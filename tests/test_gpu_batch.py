@@ -32,6 +32,8 @@ def run_gpu_batch(pkg, XT, n, Y, rmask, ratios, beta0=None, **opt):
     Md = None if rmask is None else torch.from_numpy(np.ascontiguousarray(rmask, dtype=np.uint8)).to(dev)
     r = torch.from_numpy(np.ascontiguousarray(ratios, dtype=np.float64)).to(dev)
     b0 = None if beta0 is None else torch.from_numpy(np.ascontiguousarray(beta0, dtype=np.float64)).to(dev)
+    if opt.get("gemm_dtype") == PASS:
+        opt = dict(opt, gemm_dtype=pkg.LASSO_BF16, lockstep_pass=1)
     out = pkg.solve_batch(Xd, Yd, r, n=n, row_mask=Md, beta0=b0, opts=pkg.lasso_default_opts(**opt))
     torch.cuda.synchronize()
     B, T = Y.shape[0], len(ratios)
@@ -61,8 +63,11 @@ def _subsample_problem(seed, n, p, B, frac_lo=0.4, k=5, correlated=False):
 
 # gemm_dtype 1 (LASSO_F32): every CTA runs whole paths, its checks are FP32
 # CUDA-core passes; 2 (LASSO_BF16): lockstep over lambda, the first check of
-# every lambda comes from one split-BF16 tensor-core product for all problems
-GEMM = [1, 2]
+# every lambda comes from one split-BF16 tensor-core product for all problems;
+# PASS: lockstep over coordinate passes (LASSO_BF16 with lockstep_pass = 1),
+# a product before every pass serving its check and its certificates
+PASS = 3
+GEMM = [1, 2, PASS]
 
 
 @pytest.mark.parametrize("gemm", GEMM)
@@ -202,7 +207,7 @@ def test_batch_captured_in_cuda_graph(pkg):
 
 
 def test_autotuner_picks_a_shape_and_keeps_results(pkg):
-    """lasso_batch_tune times its nine launch shapes and returns the fastest;
+    """lasso_batch_tune times its eleven launch shapes and returns the fastest;
     solving with the tuned options gives the masks and pass counts of the
     default shape (every shape makes the FP64 test's decisions) and the same
     coefficients up to rounding (a group of CTAs may run the chain in Gram
@@ -219,10 +224,13 @@ def test_autotuner_picks_a_shape_and_keeps_results(pkg):
     tuned, times = pkg.tune_batch(Xd, Yd, r, n=200, row_mask=Md, opts=base, sample=16, lambdas=4)
     assert np.all((times > 0) | (times == -1)) and np.any(times > 0)
     k = int(np.argmin(np.where(times > 0, times, np.inf)))
-    shapes = [(pkg.LASSO_F32, 2, 0, 1), (pkg.LASSO_F32, 1, 0, 1), (pkg.LASSO_BF16, 2, 128, 1),
-              (pkg.LASSO_BF16, 1, 128, 1), (pkg.LASSO_BF16, 2, 256, 1), (pkg.LASSO_BF16, 1, 256, 1),
-              (pkg.LASSO_F32, 2, 0, 8), (pkg.LASSO_F32, 2, 0, 32), (pkg.LASSO_F32, 1, 0, 16)]
-    assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n, tuned.batch_group) == shapes[k]
+    shapes = [(pkg.LASSO_F32, 2, 0, 1, 0), (pkg.LASSO_F32, 1, 0, 1, 0), (pkg.LASSO_BF16, 2, 128, 1, 0),
+              (pkg.LASSO_BF16, 1, 128, 1, 0), (pkg.LASSO_BF16, 2, 256, 1, 0), (pkg.LASSO_BF16, 1, 256, 1, 0),
+              (pkg.LASSO_F32, 2, 0, 8, 0), (pkg.LASSO_F32, 2, 0, 32, 0), (pkg.LASSO_F32, 1, 0, 16, 0),
+              (pkg.LASSO_BF16, 2, 128, 1, 1), (pkg.LASSO_BF16, 1, 128, 1, 1)]
+    assert len(times) == len(shapes)
+    assert (tuned.gemm_dtype, tuned.batch_ctas_per_sm, tuned.gemm_tile_n, tuned.batch_group,
+            tuned.lockstep_pass) == shapes[k]
     assert tuned.gap_tol_rel == 1e-9
     outs = {}
     for name, o in (("default", base), ("tuned", tuned)):
@@ -279,7 +287,7 @@ def test_batch_groups_of_ctas(pkg, group):
     check_batch(dict(beta=g["beta"][keep], mask=g["mask"][keep], stats=g["stats"][keep]), o)
 
 
-@pytest.mark.parametrize("gemm,group", [(1, 1), (2, 1), (1, 8)])
+@pytest.mark.parametrize("gemm,group", [(1, 1), (2, 1), (1, 8), (PASS, 1)])
 def test_batch_dome(pkg, gemm, group):
     """GAP SAFE dome (Eq. (11)) in every batched mode: per-CTA FP32 checks,
     lockstep split-BF16 first checks and groups of CTAs; x_j^T y is taken on
@@ -293,7 +301,7 @@ def test_batch_dome(pkg, gemm, group):
 
 
 @pytest.mark.parametrize("gemm,group,a,rule", [(1, 1, 0.5, 0), (2, 1, 0.5, 0), (1, 8, 0.7, 0), (2, 1, 0.6, 1),
-                                                (1, 1, 0.4, 1)])
+                                                (1, 1, 0.4, 1), (PASS, 1, 0.5, 0), (PASS, 1, 0.6, 1)])
 def test_batch_enet(pkg, gemm, group, a, rule):
     """The Elastic-Net in every batched mode (per-CTA FP32 checks, lockstep
     split-BF16 first checks, groups of CTAs), with the sphere or the dome:

@@ -105,14 +105,15 @@ def test_workload2_dome_every_lambda(pkg):
     _workload2(pkg, 1)
 
 
-@pytest.mark.parametrize("gemm,group", [(2, 0), (1, 0), (1, 32)])
-def test_workload3_every_problem_every_lambda(pkg, gemm, group):
+@pytest.mark.parametrize("gemm,group,per_pass", [(2, 0, 0), (1, 0, 0), (1, 32, 0), (2, 0, 1)])
+def test_workload3_every_problem_every_lambda(pkg, gemm, group, per_pass):
     """The 256 row-subset problems of the stability-selection workload
     (Gaussian 1000 x 20000, 50 lambdas to lambda_max/100), batched: lockstep
     with the split-BF16 tensor-core first check (gemm 2) and per-CTA FP32
     checks (gemm 1).  Counts, objectives, supports and masks of every
     (problem, lambda); coefficients of 16 problems spread over the batch.
-    With groups of 32 CTAs per problem the chain runs in Gram form."""
+    With groups of 32 CTAs per problem the chain runs in Gram form; with
+    per_pass = 1 the lockstep takes a product before every coordinate pass."""
     gold = _load("workload3_batch")
     w = gen.workload3()
     assert fingerprint(w["XT"]) == str(gold["x_sha256"]), "the regenerated design differs from the stored one"
@@ -126,11 +127,11 @@ def test_workload3_every_problem_every_lambda(pkg, gemm, group):
                           torch.from_numpy(gold["ratios"]).to(dev), n=n,
                           row_mask=torch.from_numpy(w["row_mask"]).to(dev),
                           opts=pkg.lasso_default_opts(screen_period=w["f"], gap_tol_rel=w["tol"], gemm_dtype=gemm,
-                                                      batch_group=group))
+                                                      batch_group=group, lockstep_pass=per_pass))
     torch.cuda.synchronize()
     st = pkg.stats_to_numpy(out["stats"]).reshape(B, T)
     beta = out["beta"].cpu().numpy()
     mask = out["mask"].cpu().numpy().view(np.uint32)
     values = set(int(v) for v in gold["values_for"])
     for b in range(B):
-        _compare(f"workload3 gemm={gemm} group={group}", beta[b], mask[b], st[b], gold, b=b, values=b in values)
+        _compare(f"workload3 gemm={gemm} group={group} per_pass={per_pass}", beta[b], mask[b], st[b], gold, b=b, values=b in values)
