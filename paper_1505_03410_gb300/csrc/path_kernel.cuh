@@ -819,6 +819,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
   __shared__ float fbuf[32];
   __shared__ int s_prob;
   __shared__ int gflags[16];
+  __shared__ int s_vnext;  // one-CTA problems: next batch of positions a verifying warp takes
 
   // G CTAs cooperate on one problem: the whole grid, or a group of the batch
   const int G = BATCH ? a.gsize : (int)gridDim.x;
@@ -1744,9 +1745,6 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               const int pos = vload(ctl->pos), rend = vload(ctl->round_end), nc = vload(ctl->nc);
               const float rb = vload(ctl->rho_bound);
               const int span = rend - pos;
-              const int gw = cta * nwarps + warp, nwg = G * nwarps;
-              const int chunk = (span + nwg - 1) / nwg;
-              const int i0 = pos + gw * chunk, i1 = min(rend, i0 + chunk);
               // one-CTA problems: D_c = ||rho_c - rho_a||, an upper bound of the
               // distance of snapshot c of the round from the anchor rho_a, and
               // their maximum.  FP32 over the high planes: the sum of squares is
@@ -1775,6 +1773,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                   if (lane == 0)
                     WS(float, dsnap)[c] = __fadd_ru(__fmul_ru(__fsqrt_ru(__fmul_ru(S, fac)), 1.0001f), abs_t);
                 }
+                if (tid == 0) s_vnext = 0;
                 __syncthreads();
                 float m = 0.f;
                 for (int c = lane; c <= nc; c += 32) m = fmaxf(m, __ldcg(WS(float, dsnap) + c));
@@ -1787,7 +1786,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                 }
               }
               unsigned long long n_scan = 0, n_read = 0, n_exact = 0;
-              if (span > 0 && i0 < i1) {
+              if (span > 0) {
                 // a zero coefficient whose certificate survives the movement of
                 // the residual since it was issued stays zero without a read:
                 // |x_j^T rho| <= lambda - slack + ||x_j|| ||rho - rho_ref|| < lambda,
@@ -1797,8 +1796,22 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                 const float mend = __ldcg(WS(float, msnap) + nc);
                 const float* skp = WS(float, sk);
                 float* mrp = WS(float, mref);
+                // positions: the group's CTAs split the window into one
+                // contiguous chunk per warp; the warps of a one-CTA problem take
+                // batches of 32 positions in ascending order from a counter in
+                // shared memory (the reads the certificates leave are unevenly
+                // spread over the window), the next batch while this one is
+                // processed.  A batch a warp holds when it stops lies past the
+                // first entering position, where no verdict is needed.
+                int i0s = pos, i1s = rend;
+                if (SP) {
+                  const int gw = cta * nwarps + warp, nwg = G * nwarps;
+                  const int chunk = (span + nwg - 1) / nwg;
+                  i0s = pos + gw * chunk;
+                  i1s = min(rend, i0s + chunk);
+                }
                 // chain entries before the current batch of positions
-                int sb = lower_bound_i(WS(int, chain), nc, i0);
+                int sb = lower_bound_i(WS(int, chain), nc, i0s);
                 float4 r4[NG];
                 int loaded = -1;
                 const float lamf = __double2float_rn(lam);
@@ -1806,7 +1819,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                 // the verdict for position i (feature j, norm nf) from its FP32
                 // correlation c with snapshot sg: stays zero (certificate
                 // renewed) or enters
-                auto decide = [&](int i, int j, float nf, float c, int sg) -> bool {
+                auto decide = [&](int i, int j, float nf, float c, int sg, float ms, float ds) -> bool {
                   const float* sh = WS(float, snap) + (size_t)sg * 2 * a.ldw;
                   const float E = __fmul_ru(__fmul_ru(bf, nf), rb) + 1e-37f;
                   bool enters;
@@ -1824,13 +1837,19 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                   } else if (lane == 0) {
                     const float slack = __fsub_rd(lam_lo, __fadd_ru(fabsf(c), E));
                     WS(float, sk)[i] = (slack > 0.f && nf > 0.f) ? __fdiv_rd(slack, nf) : kSkNone;
-                    mrp[i] = __ldcg(WS(float, msnap) + sg);
-                    if (!SP) WS(float, dref)[i] = __ldcg(WS(float, dsnap) + sg);
+                    mrp[i] = ms;
+                    if (!SP) WS(float, dref)[i] = ds;
                   }
                   return enters;
                 };
                 bool stop_warp = false;
-                for (int base = i0; base < i1 && !stop_warp; base += 32) {
+                int bidx = SP ? 0 : __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(&s_vnext, 1) : 0, 0);
+                for (;;) {
+                  const int base = i0s + 32 * bidx;
+                  if (base >= i1s || stop_warp) break;
+                  if (SP) ++bidx;
+                  else bidx = __shfl_sync(0xffffffffu, lane == 0 ? atomicAdd(&s_vnext, 1) : 0, 0);
+                  const int i1 = i1s;
                   const int il = base + lane;
                   n_scan += 32;
                   // the certificate test, with the feature of the position read
@@ -1872,6 +1891,9 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                   for (int st = 16; st > 0; st >>= 1)
                     if (__shfl_sync(0xffffffffu, ce, cnt + st - 1) < il) cnt += st;
                   const int segl = sb + cnt;
+                  // movement and distance of each needed lane's snapshot, for a renewal
+                  const float msn = need ? __ldcg(WS(float, msnap) + segl) : 0.f;
+                  const float dsn = (need && !SP) ? __ldcg(WS(float, dsnap) + segl) : 0.f;
                   while (needm) {
                     const int l = __ffs(needm) - 1;
                     needm &= needm - 1;
@@ -1882,6 +1904,7 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                     }
                     const int j = __shfl_sync(0xffffffffu, jn, l), sg = __shfl_sync(0xffffffffu, segl, l);
                     const float nf = __shfl_sync(0xffffffffu, nfn, l);
+                    const float ms = __shfl_sync(0xffffffffu, msn, l), ds = __shfl_sync(0xffffffffu, dsn, l);
                     if (loaded != sg) {
                       const float* sh = WS(float, snap) + (size_t)sg * 2 * a.ldw;
 #pragma unroll
@@ -1900,23 +1923,24 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
                     if (kPair && needm && sg2 == sg && base + l2 <= fs) {
                       const int j2 = __shfl_sync(0xffffffffu, jn, l2);
                       const float nf2 = __shfl_sync(0xffffffffu, nfn, l2);
+                      const float ms2 = __shfl_sync(0xffffffffu, msn, l2), ds2 = __shfl_sync(0xffffffffu, dsn, l2);
                       float c, c2;
                       n_read += 2;
                       warp_dot_f32_2<NG>(a.Xh + (long long)j * a.ldx, a.Xh + (long long)j2 * a.ldx, r4, a.ld4, a.n,
                                          c, c2);
-                      if (decide(i, j, nf, c, sg)) {
+                      if (decide(i, j, nf, c, sg, ms, ds)) {
                         stop_warp = true;
                         break;
                       }
                       needm &= needm - 1;
-                      if (decide(base + l2, j2, nf2, c2, sg)) {
+                      if (decide(base + l2, j2, nf2, c2, sg, ms2, ds2)) {
                         stop_warp = true;
                         break;
                       }
                     } else {
                       ++n_read;
                       const float c = warp_dot_f32<NG>(a.Xh + (long long)j * a.ldx, r4, a.ld4, a.n);
-                      if (decide(i, j, nf, c, sg)) {
+                      if (decide(i, j, nf, c, sg, ms, ds)) {
                         stop_warp = true;
                         break;
                       }
