@@ -61,7 +61,7 @@ def _args():
                          "(0 skips it), then solve --learned-eval held-out responses from zero and from the net")
     ap.add_argument("--learned-eval", type=int, default=1024, metavar="N_EVAL")
     ap.add_argument("--learned-epochs", type=int, default=10)
-    ap.add_argument("--large-sample", type=int, default=32, metavar="B",
+    ap.add_argument("--large-sample", type=int, default=16, metavar="B",
                     help="right-hand sides of the 2000 x 100000 multi-RHS workload solved by the tuned batched "
                          "solver for the large tuned-vs-plain line (0 skips it)")
     ap.add_argument("--plain-sample", type=int, default=8,
@@ -647,7 +647,7 @@ def _tuned_vs_plain_large(pkg, torch, dev, stream, flush, B, plain=2):
     plain_sps = pok / (pms / 1e3)
     shape = {"gemm_dtype": "split_bf16_tc" if tuned.gemm_dtype == pkg.LASSO_BF16 else "fp32",
              "batch_ctas_per_sm": int(tuned.batch_ctas_per_sm), "gemm_tile_n": int(tuned.gemm_tile_n),
-             "batch_group": int(tuned.batch_group)}
+             "batch_group": int(tuned.batch_group), "lockstep_pass": int(tuned.lockstep_pass)}
     return {"workload": w["name"] + ": Gaussian 2000x100000 FP32, k~U{10..200}, SNR~U[1,10], T=30 to "
                                     "lambda_max/100, check every 10 passes, gap<=1e-6*||y||^2",
             "tuned": {"solves_per_s": tuned_sps, "certified": ok, "solves": B * T, "ms": ms,
@@ -657,8 +657,9 @@ def _tuned_vs_plain_large(pkg, torch, dev, stream, flush, B, plain=2):
                                   "sample": f"first {plain} right-hand sides, one lasso_path call each"},
             "tuned_over_plain": tuned_sps / plain_sps if plain_sps > 0 else None,
             "target": ">= 5x with learned start + batched + mixed precision",
-            "note": "bounded sample of the 1024 right-hand sides so that the default bench ends in minutes; "
-                    "the learned start is measured on the 300 x 10000 workload"}
+            "note": "bounded sample of the 1024 right-hand sides so that the default bench ends in minutes (a "
+                    "sample this small leaves most SMs idle in the batched solver; --large-sample 304 runs one "
+                    "resident wave); the learned start is measured on the 300 x 10000 workload"}
 
 
 def _learned(pkg, torch, dev, stream, n_train, epochs=20, lr=1e-2, n_eval=1024):
