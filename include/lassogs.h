@@ -110,7 +110,9 @@ typedef struct lasso_opts {
                             number of launches then depends on the data: lasso_batch reads a
                             device counter of unfinished problems every 4 launches
                             (synchronising `stream`), so such a call cannot be captured in a
-                            CUDA graph */
+                            CUDA graph.  Without row_mask, the last 8 unfinished problems stop
+                            at their next lambda and finish on lasso_path's solver, one after
+                            the other (same results; the workspace holds its region) */
 } lasso_opts;
 
 /* Per-lambda record written by the solvers (device memory, one per lambda). */

@@ -138,7 +138,7 @@ size_t lasso_batch_workspace_size(int64_t n, int64_t p, int64_t B, const lasso_o
   if (opts) o = *opts;
   else lasso_default_opts(&o);
   if (check_opts(o) != LASSO_OK) return 0;
-  return batch_workspace_size(n, p, B, o.gemm_dtype == LASSO_BF16, o.batch_group);
+  return batch_workspace_size(n, p, B, o.gemm_dtype == LASSO_BF16, o.batch_group, o.lockstep_pass == 1);
 }
 
 lasso_status lasso_batch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,

@@ -30,7 +30,7 @@ lasso_status path_launch(const void* X, lasso_dtype xt, int64_t n, int64_t p, in
 lasso_status path_phase_cycles(const void* ws, uint64_t* out_host, cudaStream_t stream);
 
 // group: CTAs per problem (opts.batch_group; <= 1 for one CTA per problem)
-size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep, int group);
+size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep, int group, bool pass);
 lasso_status xtr_gemm_launch(const void* Xb, int64_t n, int64_t p, int64_t ldx, const void* Rb, int64_t ldr,
                              int64_t B, float* C, int64_t ldc, int* err_dev, cudaStream_t stream, int tile_n = 0);
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,

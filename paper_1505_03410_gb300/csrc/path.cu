@@ -2,6 +2,7 @@
 // split-BF16 operands), the workspace layout and the launches of the single
 // path and the batched solver.  The kernel itself is path_kernel.cuh.
 #include <algorithm>
+#include <vector>
 #include <cstdint>
 #include <cstdlib>
 #include <cuda_runtime.h>
@@ -524,13 +525,15 @@ struct BatchLayout {
   int grid, regions, group;
   bool lockstep;
   long long Lk;  // K segment length of the split-BF16 operands
-  size_t o_regions, o_x3, o_r3, o_c, o_gerr, total;
+  size_t o_regions, o_x3, o_r3, o_c, o_gerr, o_park, o_single, single_bytes, total;
 };
 
 // group > 1: groups of CTAs per problem, one workspace region per group (at
 // most 2 x SMs / group of them resident), each with its Gram cache when the
 // group is large enough for Gram rounds
-BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms, int group = 1) {
+// tail: lockstep per pass, whose last problems may finish on the single path
+// (the lambda at which each stopped, and the single path's own workspace)
+BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms, int group = 1, bool tail = false) {
   BatchLayout bl{};
   const bool groups = !lockstep && group > 1;
   bl.L = make_layout(n, p, kSCapBatch, false, groups && group_gram(n, group) ? kGramGroup : kGramNone);
@@ -551,6 +554,13 @@ BatchLayout batch_layout(int64_t n, int64_t p, int64_t B, bool lockstep, int sms
     off += align256(sizeof(float) * (size_t)p * (size_t)B);
     bl.o_gerr = off;
     off += 256;
+    if (tail) {
+      bl.o_park = off;
+      off += align256(sizeof(int) * (size_t)B);
+      bl.o_single = off;
+      bl.single_bytes = make_layout(n, p, kSCapPath, false, kGramSingle).total;
+      off += align256(bl.single_bytes);
+    }
   }
   bl.total = off;
   return bl;
@@ -564,9 +574,9 @@ int device_sms() {
 }
 }  // namespace
 
-size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep, int group) {
+size_t batch_workspace_size(int64_t n, int64_t p, int64_t B, bool lockstep, int group, bool pass) {
   if (n < 1 || n > kMaxRows || p < 1 || p > (int64_t)INT32_MAX / 4 || B < 1) return 0;
-  return batch_layout(n, p, B, lockstep, device_sms(), group).total;
+  return batch_layout(n, p, B, lockstep, device_sms(), group, lockstep && pass).total;
 }
 
 lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, const double* Y, int64_t ldy,
@@ -578,7 +588,7 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
   lasso_status st = dev_info(d);
   if (st != LASSO_OK) return st;
   const bool lockstep = o.gemm_dtype == LASSO_BF16;
-  const BatchLayout bl = batch_layout(n, p, B, lockstep, d.sms, o.batch_group);
+  const BatchLayout bl = batch_layout(n, p, B, lockstep, d.sms, o.batch_group, lockstep && o.lockstep_pass == 1);
   if (ws_bytes < bl.total)
     return set_error(LASSO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu bytes required", ws_bytes,
                      bl.total);
@@ -671,6 +681,18 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
     CUDA_TRY(cudaGetLastError());
     a.pass_mode = 1;
     a.active = active;
+    // the tail: once at most kParkAt problems are unfinished, each stops at its
+    // next lambda boundary and the rest of its path runs on the single path,
+    // whose launch uses every SM for one problem (its iterates from a lambda
+    // boundary on are those of the path: the warm start carries beta, and the
+    // check that starts the next lambda is the path's own).  Row subsets have
+    // no single-path form, so such batches finish in lockstep.
+    constexpr int kParkAt = 8;
+    int* park_t = reinterpret_cast<int*>(base + bl.o_park);
+    CUDA_TRY(cudaMemsetAsync(park_t, 0xff, sizeof(int) * (size_t)B, stream));
+    a.park = 0;
+    a.park_t = park_t;
+    bool parked = false;
     const long long max_launches = (long long)T * (o.max_epochs + 1) + 1;
     for (long long step = 0; step < max_launches; ++step) {
       const bool use_gemm = !(step == 0 && beta0 != nullptr);
@@ -692,6 +714,28 @@ lasso_status batch_launch(const float* X, int64_t n, int64_t p, int64_t ldx, con
         CUDA_TRY(cudaMemcpyAsync(&left, active, sizeof(int), cudaMemcpyDeviceToHost, stream));
         CUDA_TRY(cudaStreamSynchronize(stream));
         if (left <= 0) break;
+        if (left <= kParkAt && row_mask == nullptr && !parked) {
+          parked = true;
+          a.park = 1;
+        }
+      }
+    }
+    if (parked) {
+      std::vector<int> pt((size_t)B);
+      CUDA_TRY(cudaMemcpyAsync(pt.data(), park_t, sizeof(int) * (size_t)B, cudaMemcpyDeviceToHost, stream));
+      CUDA_TRY(cudaStreamSynchronize(stream));
+      const int64_t words = (p + 31) / 32;
+      for (int64_t b = 0; b < B; ++b) {
+        const int t = pt[(size_t)b];
+        if (t < 1 || t >= T) continue;
+        // warm start: the solution of lambda_{t-1}; else every lambda restarts from beta0
+        const double* b0 = o.warm_start ? beta_out + (size_t)p * ((size_t)(t - 1) + (size_t)T * (size_t)b)
+                                        : (beta0 != nullptr ? beta0 + (size_t)b * (size_t)ldb0 : nullptr);
+        const size_t off = (size_t)t + (size_t)T * (size_t)b;
+        st = path_launch(X, LASSO_F32, n, p, ldx, Y + (size_t)b * (size_t)ldy, ratios + t, T - t, b0, o,
+                         beta_out + (size_t)p * off, mask_out != nullptr ? mask_out + (size_t)words * off : nullptr,
+                         stats + off, base + bl.o_single, bl.single_bytes, stream);
+        if (st != LASSO_OK) return st;
       }
     }
     return LASSO_OK;

@@ -139,6 +139,11 @@ struct Args {
   // problems whose path is not finished
   int pass_mode;
   int* active;
+  // park: a problem that finishes a lambda stops there and records the next
+  // lambda in park_t[b] (the host solves the rest of its path on the single
+  // path); set for the last few unfinished problems of a batch without row subsets
+  int park;
+  int* park_t;
   const float* cfirst;
   long long ldc;
   float cfactor;
@@ -2096,6 +2101,15 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
     // the lambda is finished: a later lambda of this launch starts afresh
     resume = false;
     if (PM && cta == 0 && tid == 0) ctl->resume = 0;
+    if (PM && a.park && t + 1 < t_end) {
+      if (tid == 0) {
+        ctl->pdone = 1;
+        a.park_t[b] = t + 1;
+        atomicSub(a.active, 1);
+      }
+      __syncthreads();
+      goto pass_exit;
+    }
   }  // lambda loop
   if (PM && tid == 0) {
     ctl->pdone = 1;

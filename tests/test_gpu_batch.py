@@ -327,3 +327,25 @@ def test_batch_refined_radius(pkg, gemm):
     g = run_gpu_batch(pkg, prob["XT"], 120, Y, rmask, ratios, beta0=beta0, gemm_dtype=gemm, **opt)
     o = oracle.lasso_batch(prob["XT"], Y * rmask, ratios, row_mask=rmask, n=120, beta0=beta0, **opt)
     check_batch(g, o)
+
+
+@pytest.mark.parametrize("warm,a", [(1, 1.0), (0, 1.0), (1, 0.6)])
+def test_batch_pass_tail_on_single_path(pkg, warm, a):
+    """Lockstep per pass on a batch without row subsets: once at most 8
+    problems are unfinished, each stops at its next lambda boundary and the
+    rest of its path runs on the single path.  Every (problem, lambda) still
+    equals the oracle: passes, checks, masks, objectives, coefficients; with
+    warm starts off the single path restarts every lambda from beta0 too."""
+    prob = gen.small_problem(212, 120, 1500, dtype=np.float32, k=8, correlated=True)
+    rng = np.random.default_rng(212)
+    B = 7
+    Y = np.stack([prob["y"] * rng.uniform(0.5, 2.0) + 0.3 * rng.standard_normal(120) for _ in range(B)])
+    beta0 = np.zeros((B, 1500))
+    for b in range(0, B, 2):
+        idx = rng.choice(1500, size=12, replace=False)
+        beta0[b, idx] = 0.2 * rng.standard_normal(12)
+    ratios = oracle.lambda_ratios(12, 2.0)[1:]
+    opt = dict(gap_tol_rel=1e-9, warm_start=warm, enet_alpha=a)
+    g = run_gpu_batch(pkg, prob["XT"], 120, Y, None, ratios, beta0=beta0, gemm_dtype=PASS, **opt)
+    o = oracle.lasso_batch(prob["XT"], Y, ratios, n=120, beta0=beta0, **opt)
+    check_batch(g, o)
