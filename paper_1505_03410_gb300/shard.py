@@ -31,14 +31,32 @@ def _world(group):
     return 1, 0
 
 
+def _sparse_block(beta):
+    """The nonzeros of a (B_r, T, p) coefficient block: flat indices (int64)
+    into the block and their values; a Lasso solution has at most n nonzeros
+    per lambda, so this is far smaller than the dense block."""
+    flat = beta.reshape(-1)
+    idx = np.flatnonzero(flat)
+    return idx.astype(np.int64), flat[idx]
+
+
 def solve_batch_sharded(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=None, group=None, dst=0,
-                        solver=None):
+                        solver=None, beta_format="sparse"):
     """Solve the B problems of (Y, row_mask, beta0) -- the layouts of
     ``solve_batch`` -- split over the ranks of `group`, each rank on its own
-    GPU.  Returns, on rank `dst`, host arrays for the whole batch: beta
-    (B, T, p) float64, mask (B, T, words) uint32 and stats, a structured array
-    (B, T) of ``STATS_DTYPE``; on the other ranks, None.  `solver` replaces
-    ``solve_batch`` (same signature and outputs), e.g. to add options."""
+    GPU.  Returns, on rank `dst`, host arrays for the whole batch: beta, mask
+    (B, T, words) uint32 and stats, a structured array (B, T) of
+    ``STATS_DTYPE``; on the other ranks, None.
+
+    beta_format: "sparse" (default) gathers only the nonzero coefficients and
+    returns beta as a scipy.sparse CSR matrix of shape (B * T, p), row
+    b * T + t holding problem b's solution at lambda_t; "dense" gathers the
+    full (B, T, p) float64 array (B * T * p * 8 bytes through host memory:
+    about 25 GB for 1024 problems, 30 lambdas and 100000 features).
+    `solver` replaces ``solve_batch`` (same signature and outputs), e.g. to
+    add options."""
+    if beta_format not in ("sparse", "dense"):
+        raise ValueError(f"beta_format must be 'sparse' or 'dense', not {beta_format!r}")
     import torch.distributed as dist
     solver = solver or solve_batch
     world, rank = _world(group)
@@ -51,12 +69,14 @@ def solve_batch_sharded(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=N
         out = solver(XT, Y[a:b].contiguous(), ratios, n=n,
                      row_mask=row_mask[a:b].contiguous() if row_mask is not None else None,
                      beta0=beta0[a:b].contiguous() if beta0 is not None else None, opts=opts)
-        local = (a, out["beta"].cpu().numpy(),
+        beta_np = out["beta"].cpu().numpy()
+        local = (a, _sparse_block(beta_np) if beta_format == "sparse" else beta_np,
                  out["mask"].cpu().numpy().view(np.uint32) if out.get("mask") is not None else None,
                  out["stats"].cpu().numpy().view(STATS_DTYPE).reshape(b - a, T))
     else:
-        local = (a, np.empty((0, T, p)), np.empty((0, T, words), dtype=np.uint32),
-                 np.empty((0, T), dtype=STATS_DTYPE))
+        empty = np.empty((0, T, p))
+        local = (a, _sparse_block(empty) if beta_format == "sparse" else empty,
+                 np.empty((0, T, words), dtype=np.uint32), np.empty((0, T), dtype=STATS_DTYPE))
     if world == 1:
         parts = [local]
     else:
@@ -65,10 +85,18 @@ def solve_batch_sharded(XT, Y, ratios, n=None, row_mask=None, beta0=None, opts=N
         if rank != dst:
             return None
     parts.sort(key=lambda t: t[0])
-    beta = np.concatenate([t[1] for t in parts], axis=0)
     stats = np.concatenate([t[3] for t in parts], axis=0)
     mask = None
     if all(t[2] is not None for t in parts):
         mask = np.concatenate([t[2] for t in parts], axis=0)
-    assert beta.shape[0] == B and stats.shape[0] == B
+    assert stats.shape[0] == B
+    if beta_format == "dense":
+        beta = np.concatenate([t[1] for t in parts], axis=0)
+        assert beta.shape[0] == B
+    else:
+        import scipy.sparse as sp
+        # a rank's flat index (b_local * T + t) * p + j, shifted by its first problem
+        idx = np.concatenate([t[1][0] + t[0] * T * p for t in parts])
+        val = np.concatenate([t[1][1] for t in parts])
+        beta = sp.csr_matrix((val, (idx // p, idx % p)), shape=(B * T, p))
     return dict(beta=beta, mask=mask, stats=stats)

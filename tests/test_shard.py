@@ -59,18 +59,46 @@ def _inputs(B=7, n=5, p=40, T=3):
 def _check_full(out, B=7, n=5, p=40, T=3):
     XT, Y, rm, ratios = _inputs(B, n, p, T)
     ref = fake_solver(XT, Y, ratios, row_mask=rm)
-    np.testing.assert_array_equal(out["beta"], ref["beta"].numpy())
+    beta = out["beta"]
+    if not isinstance(beta, np.ndarray):  # the sparse gather: rows b * T + t
+        assert beta.shape == (B * T, p)
+        beta = beta.toarray().reshape(B, T, p)
+    np.testing.assert_array_equal(beta, ref["beta"].numpy())
     np.testing.assert_array_equal(out["stats"]["lambda"], Y[:, 0].numpy()[:, None].repeat(T, 1))
     np.testing.assert_array_equal(out["stats"]["status"], rm.numpy().sum(axis=1)[:, None].repeat(T, 1))
     assert out["mask"].shape == (B, T, 2) and np.all(out["mask"] == 7)
 
 
-def test_single_process_is_the_whole_batch():
+@pytest.mark.parametrize("fmt", ["sparse", "dense"])
+def test_single_process_is_the_whole_batch(fmt):
     XT, Y, rm, ratios = _inputs()
-    _check_full(solve_batch_sharded(XT, Y, ratios, row_mask=rm, solver=fake_solver))
+    out = solve_batch_sharded(XT, Y, ratios, row_mask=rm, solver=fake_solver, beta_format=fmt)
+    assert isinstance(out["beta"], np.ndarray) == (fmt == "dense")
+    _check_full(out)
 
 
-def _worker(rank, world, port, q, B):
+def test_sparse_gather_keeps_zeros_out():
+    """The sparse form holds exactly the nonzero coefficients."""
+    XT, Y, rm, ratios = _inputs(B=3, p=40, T=2)
+
+    def solver(*args, **kw):
+        out = fake_solver(*args, **kw)
+        beta = out["beta"].numpy().copy()
+        beta[:, :, ::3] = 0.0
+        return dict(out, beta=torch.from_numpy(beta))
+    out = solve_batch_sharded(XT, Y, ratios, row_mask=rm, solver=solver)
+    dense = solver(XT, Y, ratios, row_mask=rm)["beta"].numpy()
+    assert out["beta"].nnz == int(np.count_nonzero(dense))
+    np.testing.assert_array_equal(out["beta"].toarray().reshape(dense.shape), dense)
+
+
+def test_bad_beta_format_is_rejected():
+    XT, Y, rm, ratios = _inputs()
+    with pytest.raises(ValueError):
+        solve_batch_sharded(XT, Y, ratios, solver=fake_solver, beta_format="csr")
+
+
+def _worker(rank, world, port, q, B, fmt="sparse"):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
@@ -78,21 +106,21 @@ def _worker(rank, world, port, q, B):
     try:
         from paper_1505_03410_gb300.shard import solve_batch_sharded as sbs
         XT, Y, rm, ratios = _inputs(B=B)
-        out = sbs(XT, Y, ratios, row_mask=rm, solver=fake_solver)
+        out = sbs(XT, Y, ratios, row_mask=rm, solver=fake_solver, beta_format=fmt)
         q.put((rank, None if out is None else (out["beta"], out["stats"], out["mask"])))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("B", [7, 1])
-def test_two_gloo_ranks_gather_the_whole_batch(B):
+@pytest.mark.parametrize("B,fmt", [(7, "sparse"), (1, "sparse"), (7, "dense")])
+def test_two_gloo_ranks_gather_the_whole_batch(B, fmt):
     """Rank 0 ends with every problem's outputs in order; rank 1 with None.
     With B = 1 the second rank has no problem and still takes part."""
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    port = 29631 + B
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, B)) for r in range(2)]
+    port = 29631 + B + (8 if fmt == "dense" else 0)
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, B, fmt)) for r in range(2)]
     for pr in procs:
         pr.start()
     res = dict(q.get(timeout=120) for _ in range(2))
