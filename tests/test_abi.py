@@ -178,6 +178,36 @@ def test_enet_alpha_out_of_range(pkg, a):
     assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("v", [-1, 2])
+def test_lockstep_pass_out_of_range(pkg, v):
+    """lockstep_pass is 0 or 1; the host rejects the rest before any CUDA
+    call, and the workspace query answers 0 for it."""
+    o = pkg.lasso_default_opts(lockstep_pass=v)
+    with pytest.raises(pkg.LassoError) as e:
+        pkg.lasso_batch(1 << 12, 10, 20, 12, 1 << 12, 10, None, 0, 2, 1 << 12, 3, None, 0, o, 1 << 12, None,
+                        1 << 12, 1 << 12, 1 << 20, None)
+    assert e.value.status == pkg.LASSO_ERR_INVALID_ARG
+    assert "lockstep_pass" in pkg.lasso_last_error()
+    assert pkg.lasso_batch_workspace_size(10, 20, 2, o) == 0
+
+
+def test_pass_lockstep_workspace_holds_the_single_path_region(pkg):
+    """Lockstep per pass may finish its last problems on the single path, so
+    its workspace holds a single-path region (at least lasso_path's own
+    workspace) on top of the per-lambda lockstep's."""
+    n, p, B = 500, 3000, 40
+    per_lambda = pkg.lasso_batch_workspace_size(n, p, B, pkg.lasso_default_opts(gemm_dtype=pkg.LASSO_BF16))
+    per_pass = pkg.lasso_batch_workspace_size(n, p, B, pkg.lasso_default_opts(gemm_dtype=pkg.LASSO_BF16,
+                                                                              lockstep_pass=1))
+    single = pkg.lasso_path_workspace_size(n, p, pkg.LASSO_F32)
+    assert per_lambda > 0 and single > 0
+    assert per_pass >= per_lambda + single
+    # the option only matters for lockstep batches
+    f32 = pkg.lasso_default_opts(gemm_dtype=pkg.LASSO_F32)
+    f32p = pkg.lasso_default_opts(gemm_dtype=pkg.LASSO_F32, lockstep_pass=1)
+    assert pkg.lasso_batch_workspace_size(n, p, B, f32) == pkg.lasso_batch_workspace_size(n, p, B, f32p)
+
+
 def test_struct_layouts_match_the_header(pkg, tmp_path):
     """The ctypes mirrors of lasso_opts and lasso_path_stats have the field
     offsets and sizes a C compiler gives the declarations in lassogs.h."""
