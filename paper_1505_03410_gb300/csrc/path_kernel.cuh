@@ -1750,12 +1750,13 @@ __global__ void __launch_bounds__(kThreads, MINB) path_kernel(Args a) {
               const int pos = vload(ctl->pos), rend = vload(ctl->round_end), nc = vload(ctl->nc);
               const float rb = vload(ctl->rho_bound);
               const int span = rend - pos;
-              // one-CTA problems: D_c = ||rho_c - rho_a||, an upper bound of the
+              // one-CTA problems: D_c >= ||rho_c - rho_a||, a bound on the
               // distance of snapshot c of the round from the anchor rho_a, and
-              // their maximum.  FP32 over the high planes: the sum of squares is
-              // enlarged by its accumulation error ((terms per lane + 8) 2^-23),
-              // and 2^-22 (||rho_c|| + ||rho_a||) covers the dropped low planes
-              // (each below 2^-24 of its high plane) and the differences' rounding
+              // the largest of them.  FP32 over the high planes: the sum of
+              // squares is enlarged by its accumulation error ((terms per lane
+              // + 8) 2^-23), its root by 1e-4 (the differences' rounding), and
+              // 2^-22 (||rho_c|| + ||rho_a||) covers the dropped low planes (each
+              // below 2^-24 of its high plane)
               float dmax = 3.0e38f;
               const long long td0 = clock64();
               if (!SP) {
